@@ -1,0 +1,339 @@
+"""Benchmark: range-gate spectra per second of the fused integrator at nfft = 16384.
+
+A step is one integration of the realistic workload through the C ABI: isr_integrate
+over all IPPs (decode -> FFT -> |X|^2 accumulate, chunk reduction) followed by
+isr_spectra into a device buffer.  The echo is generated on the device before timing
+(1.66 GB of int16 IQ, larger than L2, so no flush is needed between steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (under torchrun) every rank integrates its own block of range gates (an
+independent problem of the same size: weak scaling, no data-path collective); rank 0
+prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on host cores on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "range-gate spectra/sec (nfft=16384)"
+UNIT = "spectra/s"
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def _workload(name, rank):
+    import synth
+    if name == "small":
+        return synth.small(seed=1 + 1000 * rank)
+    if name == "paper":
+        return synth.paper(seed=3 + 1000 * rank)
+    return synth.realistic(seed=2 + 1000 * rank)
+
+
+def _workload_desc(w):
+    return (f"{w.name}: {w.n_ranges} gates x nfft {w.nfft} x {w.n_ipp} IPPs, gate step {w.range_step}, "
+            f"echo row {w.echo_stride} int16 IQ samples, binary-phase code {w.code_len}, "
+            f"{'Langmuir lines' if w.kind == 2 else 'tones'} at SNR {w.snr_db:g} dB per gate")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.fh = None
+
+    def start(self):
+        try:
+            self.fh = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu_id], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.seek(0)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.fh:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        busy = [s for s, p in zip(sm, power) if p > 0.25 * max(power)] if power else sm
+        return {"sm_mhz": statistics.median(busy) if busy else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def _gpu_selector(torch, dev_index):
+    try:
+        u = str(torch.cuda.get_device_properties(dev_index).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[dev_index] if vis else str(dev_index)
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _cpu_sample(w, n_gates, n_ipp, threads):
+    """Time the FP64 oracle on n_gates gates (spread over the workload) x n_ipp IPPs."""
+    import numpy as np
+
+    import oracle
+    echo = w.echo_host(0, n_ipp, n_threads=threads)
+    code = w.code()
+    sel = np.unique(np.linspace(0, w.n_ranges - 1, n_gates).astype(np.int32))
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.integrate(echo, code, nfft=w.nfft, n_ranges=w.n_ranges, range_start=w.range_start,
+                     range_step=w.range_step, sel=sel, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return len(sel) * n_ipp / dt, len(sel), dt
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    w = _workload(args.workload, 0)
+    gates, ipps = args.ref_gates, args.ref_ipps
+    for _ in range(args.warmup):
+        _cpu_sample(w, gates, ipps, threads)
+    rates, secs = [], 0.0
+    for _ in range(args.steps):
+        r, ng, dt = _cpu_sample(w, gates, ipps, threads)
+        rates.append(r)
+        secs += dt
+    value = len(rates) * ng * ipps / secs
+    sample = f"{ng} gates spread over the workload x the first {ipps} IPPs per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Philox echoes)",
+            "config": {"workload": _workload_desc(w), "nfft": w.nfft, "n_ranges": w.n_ranges, "n_ipp": w.n_ipp},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2311_18737_gb300 import isr
+
+    world, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = _workload(args.workload, rank)
+    R, N, P = w.n_ranges, w.nfft, w.n_ipp
+    echo = torch.empty((P, w.echo_stride, 2), dtype=torch.int16, device=dev)
+    code_d = torch.from_numpy(w.code()).to(dev)
+    w.echo_device(echo.data_ptr(), code_d.data_ptr())
+    stream = torch.cuda.Stream(dev)
+    out = torch.empty((R, N), dtype=torch.float32, device=dev)
+
+    plan = isr.Plan(nfft=N, n_ranges=R, echo_stride=w.echo_stride, range_start=w.range_start,
+                    range_step=w.range_step, tx_type=isr.ISR_TX_PM1, device=local, stream=stream)
+    plan.set_profiling(True)
+
+    def step(e, c, o):
+        plan.integrate(e, c, P)
+        plan.spectra(o, isr.ISR_RESET_AFTER)
+
+    for _ in range(max(3, args.warmup)):
+        step(echo, code_d, out)
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(_gpu_selector(torch, local))
+    sampler.start()
+    time.sleep(0.3)
+    info0 = plan.info()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(echo, code_d, out)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    info1 = plan.info()
+    clocks = sampler.stop()
+
+    launches = info1["kernel_launches"] - info0["kernel_launches"]
+    timed = info1["kernel_timed"] - info0["kernel_timed"]
+    kernel_ms = (info1["kernel_ms"] - info0["kernel_ms"]) / max(1, timed)
+    launches_per_step = launches / args.steps
+    # our kernels per step: fused kernel + reduction per launch block, one conversion
+    gpu_launches = int(launches * 2 + args.steps)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timing
+    e2e = None
+    if not args.no_e2e:
+        echo_h = torch.empty(echo.shape, dtype=torch.int16, pin_memory=True)
+        echo_h.copy_(echo)
+        code_h = code_d.cpu().pin_memory()
+        out_h = torch.empty((R, N), dtype=torch.float32, pin_memory=True)
+        step(echo_h, code_h, out_h)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            step(echo_h, code_h, out_h)
+        e2e_ms = 1000 * (time.perf_counter() - t0) / args.e2e_steps
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * R * P / (e2e_ms / 1000), "unit": UNIT,
+               "h2d_bytes_per_step": int(echo_h.numel() * 2 + code_h.numel()),
+               "d2h_bytes_per_step": int(out_h.numel() * 4), "ms_per_step": e2e_ms}
+        del echo_h
+
+    if world > 1:
+        t = torch.tensor([ms, kernel_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, kernel_ms = float(t[0].item()), float(t[1].item())
+
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    fp32_peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flops_per_transform = 5.0 * N * math.log2(N)
+    transforms_per_launch = R * P / max(1.0, launches_per_step)
+    achieved = flops_per_transform * transforms_per_launch / (kernel_ms / 1000) / 1e12 if kernel_ms > 0 else None
+    traffic = _recorded_traffic(N)
+
+    line = {"metric": METRIC, "value": world * R * P / (ms / 1000), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Philox echoes generated on the device, not timed)",
+            "config": {"workload": _workload_desc(w), "nfft": N, "n_ranges": R, "n_ipp": P,
+                       "gates_per_rank": R, "l2": "inputs larger than L2 (echo %.2f GB per step)" % (
+                           echo.numel() * 2 / 1e9), "kernel": "fused decode+FFT+|X|^2, chunks of %d IPPs" %
+                       plan.info()["ipp_chunk"]},
+            "gpu_launches": gpu_launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                         "frac": (achieved / fp32_peak_tflops) if achieved else None, "traffic": traffic,
+                         "peak_basis": "derived FP32 SIMT peak: %d SMs x %d lanes x 2 FLOP x %.0f MHz (sm max)"
+                                       % (props.multi_processor_count, FP32_LANES_PER_SM, sm_max),
+                         "flop_model": "5 N log2 N per transform", "kernel_ms_per_launch": kernel_ms},
+            "clocks": clocks, "e2e": e2e}
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        v, ng, dt = _cpu_sample(w, args.ref_gates, args.ref_ipps, threads)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"{ng} gates spread over the workload x the first {args.ref_ipps} IPPs "
+                                          f"({dt:.1f} s wall)"}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def _recorded_traffic(nfft):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (else null)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2311_18737_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    if rec.get("kernel_source_sha256") != h.hexdigest():
+        return None
+    return rec.get("bytes_per_launch", {}).get(str(nfft))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["realistic", "small", "paper"], default="realistic")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-gates", type=int, default=64)
+    ap.add_argument("--ref-ipps", type=int, default=64)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

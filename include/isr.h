@@ -1,0 +1,158 @@
+/*
+ * isr.h -- C ABI of the GB300 plasma-line spectrum integrator.
+ *
+ * Operation (Hilliard, Vierinen & Erickson, "GPGPU Acceleration of Incoherent Scatter
+ * Radar Plasma Line Analysis", Sec. 2.2 Eqs. 7-8 and Sec. 3.2): for every inter-pulse
+ * period (IPP) p and every range gate r, with window start s_r = start + r * step,
+ *
+ *     x[k]    = conj(eps_p[k]) * m_p[s_r + k]          (k < code_len; zero up to nfft)
+ *     X[f]    = sum_k x[k] exp(-2 pi i f k / nfft)     (forward, unnormalised, bins 0..nfft-1)
+ *     A[r][f] += |X[f]|^2                              (sum over IPPs)
+ *
+ * The decode multiply, the transform and the power accumulation run fused in one kernel
+ * on the GPU; decoded batches never leave the SM.  All calls return an isr_status; on
+ * failure isr_last_error() gives a one-line reason (per calling thread).  No C++
+ * exception crosses this interface.  Device pointers are plain CUDA device addresses
+ * (for example torch tensor data_ptr()); streams are cudaStream_t passed as void*.
+ */
+#ifndef ISR_H
+#define ISR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ISR_OK = 0,
+    ISR_ERR_INVALID_ARG = 1,  /* NULL pointer, bad size, misaligned buffer, n_ipp < 0 ...   */
+    ISR_ERR_UNSUPPORTED = 2,  /* nfft not a power of two in [8, 16384], unknown tx type     */
+    ISR_ERR_OUT_OF_RANGE = 3, /* a gate's window runs past the end of an echo row           */
+    ISR_ERR_NO_MEMORY = 4,    /* device or host allocation failed                            */
+    ISR_ERR_CUDA = 5,         /* a CUDA call or kernel launch failed (see isr_last_error)    */
+    ISR_ERR_TIMEOUT = 6       /* a kernel gave up waiting for its staged input; the result
+                                 of that integration is incomplete                          */
+} isr_status;
+
+/* Transmit-code chip formats. */
+typedef enum {
+    ISR_TX_CI16 = 0, /* complex int16: interleaved (I, Q), 4 bytes per chip             */
+    ISR_TX_C32 = 1,  /* complex float: interleaved (re, im), 8 bytes per chip           */
+    ISR_TX_PM1 = 2   /* binary phase: one int8 per chip, -1 where negative, else +1     */
+} isr_tx_type;
+
+/* Plan description.  Geometry is fixed for the life of a plan. */
+typedef struct {
+    int32_t nfft;        /* transform length: power of two, 8 <= nfft <= 16384 (Sec. 3.2.2) */
+    int32_t code_len;    /* chips per code, 1 <= code_len <= nfft; the window is zero-padded */
+    int32_t n_ranges;    /* R range gates, >= 1                                               */
+    int32_t range_start; /* s_0 in samples, >= 0                                              */
+    int32_t range_step;  /* gate spacing in samples, >= 1 (Sec. 4: 25)                        */
+    int32_t tx_type;     /* isr_tx_type                                                       */
+    int64_t echo_stride; /* complex samples per echo row (IPP); multiple of 4                 */
+    int64_t tx_stride;   /* chips between per-IPP code rows; 0 = one code for every IPP       */
+    int32_t ipp_chunk;   /* max IPPs summed in FP32 before the FP64 reduction; 0 = 256        */
+    int32_t max_chunks;  /* IPP chunks in flight per launch (scratch = max_chunks * R * nfft
+                            floats); 0 = automatic (<= 64, <= 4 GiB)                          */
+    int32_t device;      /* CUDA device ordinal; -1 = the calling thread's current device     */
+    int32_t flags;       /* reserved, must be 0                                               */
+    void* stream;        /* cudaStream_t for all work of this plan; NULL = legacy default     */
+} isr_plan_desc;
+
+/* Optional per-call gate geometry (overrides the plan's start and step for one call). */
+typedef struct {
+    int32_t start;
+    int32_t step;
+    int32_t count; /* must equal the plan's n_ranges */
+} isr_ranges;
+
+/* Flags of isr_spectra. */
+#define ISR_RESET_AFTER 1 /* zero the accumulators (and the IPP count) after reading them */
+#define ISR_MEAN 2        /* divide by the number of integrated IPPs (Eq. 8's mean)       */
+
+/* Read-only plan facts, for callers that size buffers or report launch shapes. */
+typedef struct {
+    int32_t nfft;
+    int32_t n_ranges;
+    int32_t ranges_per_cta;    /* gates one CTA transforms side by side */
+    int32_t threads_per_cta;
+    int32_t smem_bytes;        /* dynamic shared memory per CTA */
+    int32_t max_chunks;
+    int32_t ipp_chunk;
+    int32_t sm_count;
+    int64_t n_ipp_integrated;  /* IPPs summed since creation or the last reset */
+    int64_t kernel_launches;   /* fused-kernel launches since creation */
+    double kernel_ms;          /* summed fused-kernel time of timed launches (profiling) */
+    int64_t kernel_timed;      /* launches counted in kernel_ms */
+} isr_plan_info;
+
+typedef struct isr_plan isr_plan;
+
+/*
+ * Create a plan: validates the description and allocates, on the plan's device, the
+ * persistent [n_ranges][nfft] accumulators (FP64, zeroed) and the IPP-chunk scratch.
+ * The plan owns that memory until isr_destroy.  On failure *out is set to NULL.
+ * Errors: ISR_ERR_INVALID_ARG, ISR_ERR_UNSUPPORTED, ISR_ERR_OUT_OF_RANGE (the last gate's
+ * window, range_start + (n_ranges-1)*range_step + code_len, exceeds echo_stride),
+ * ISR_ERR_NO_MEMORY, ISR_ERR_CUDA.
+ */
+isr_status isr_plan_create(isr_plan** out, const isr_plan_desc* desc);
+
+/*
+ * Add n_ipp IPPs to the plan's accumulators (Eqs. 7-8; the paper's kernel pipeline of
+ * Sec. 3.2 fused into one launch).  Repeated calls continue one integration.
+ *   echo    : int16 [n_ipp][echo_stride][2] (I, Q), 16-byte aligned.  Device memory: the
+ *             call is asynchronous on the plan's stream and the caller keeps echo and
+ *             tx_code alive until the stream passes.  Host memory (pageable or pinned):
+ *             the call streams the rows to the GPU through plan-owned staging buffers,
+ *             overlapping copies with the kernels, and returns when the host buffers
+ *             may be reused.
+ *   tx_code : the code(s) in the plan's tx_type, [1 or n_ipp rows] with row p at
+ *             p * tx_stride chips; same memory kind rules as echo.
+ *   ranges  : NULL = the plan's (range_start, range_step); else that geometry for this
+ *             call (count must equal n_ranges; window bounds are re-checked).
+ *   nfft    : must equal the plan's nfft (guards against mixing plans).
+ * n_ipp == 0 is a no-op.  Arguments are checked on the host before anything is
+ * launched.  Errors: ISR_ERR_INVALID_ARG, ISR_ERR_OUT_OF_RANGE, ISR_ERR_NO_MEMORY,
+ * ISR_ERR_CUDA.
+ */
+isr_status isr_integrate(isr_plan* plan, const int16_t* echo, const void* tx_code, int32_t n_ipp,
+                         const isr_ranges* ranges, int32_t nfft);
+
+/*
+ * Synchronise the plan's stream and copy the [n_ranges][nfft] spectra, as float, to out
+ * (device or host memory, caller-owned).  flags: ISR_MEAN divides by the IPP count
+ * (no-op when it is 0), ISR_RESET_AFTER zeroes the accumulators afterwards.
+ * *n_ipp_out (optional) receives the number of IPPs integrated.  Returns
+ * ISR_ERR_TIMEOUT if any kernel since the last call reported a timed-out wait.
+ */
+isr_status isr_spectra(isr_plan* plan, float* out, int32_t flags, int64_t* n_ipp_out);
+
+/* Fill *info with the plan's launch shape and counters.  Does not synchronise. */
+isr_status isr_plan_query(const isr_plan* plan, isr_plan_info* info);
+
+/* Turn per-launch CUDA-event timing of the fused kernel on (1) or off (0). */
+isr_status isr_plan_set_profiling(isr_plan* plan, int32_t enable);
+
+/* Bound of every wait on a staged echo window, in mbarrier polls (default 2^22, on the
+ * order of a second).  A wait that runs out makes the kernel stop, record the failure
+ * and return; the next isr_spectra reports ISR_ERR_TIMEOUT.  polls must be > 0. */
+isr_status isr_plan_set_wait_limit(isr_plan* plan, uint32_t polls);
+
+/* Test hook: the kernels of the following isr_integrate calls never stage the window of
+ * IPP `ipp` (counted from the first IPP of each call; -1 turns the hook off), so its wait
+ * runs out and exercises the timeout path above without any fault. */
+isr_status isr_plan_test_drop_window(isr_plan* plan, int32_t ipp);
+
+/* Release the plan and its device memory (synchronises its stream first); NULL is safe. */
+void isr_destroy(isr_plan* plan);
+
+/* Reason for the last failed call made by this thread ("" if none). */
+const char* isr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISR_H */

@@ -1,0 +1,144 @@
+// isr_fft.cuh -- register-resident radix-R DFT building blocks for the fused kernel.
+//
+// The transform of the paper's Sec. 3.2.2 (a length-nfft forward DFT per decoded window)
+// is computed as a Stockham sequence of radix-R passes; each pass applies R-point DFTs
+// held entirely in registers.  Every index below is a compile-time constant after
+// template expansion, so the arrays live in registers and bit reversal is free.
+#pragma once
+
+#include <cstdint>
+#include <utility>
+
+namespace isr {
+
+// ---------------------------------------------------------------- compile-time helpers
+template <int... Is, class F>
+__device__ __forceinline__ void sfor_impl(std::integer_sequence<int, Is...>, F&& f)
+{
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+
+// f(integral_constant<int, 0>) ... f(integral_constant<int, N-1>)
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    sfor_impl(std::make_integer_sequence<int, N>{}, f);
+}
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+
+__host__ __device__ constexpr int bitrev(int x, int bits)
+{
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+
+// Taylor series on |x| <= pi/4, evaluated by the compiler in double.
+__host__ __device__ constexpr double ct_sin_small(double x)
+{
+    double x2 = x * x, p = 1.0;
+    for (int k = 10; k >= 1; --k) p = 1.0 - x2 / double((2 * k) * (2 * k + 1)) * p;
+    return x * p;
+}
+__host__ __device__ constexpr double ct_cos_small(double x)
+{
+    double x2 = x * x, p = 1.0;
+    for (int k = 10; k >= 1; --k) p = 1.0 - x2 / double((2 * k - 1) * (2 * k)) * p;
+    return p;
+}
+
+constexpr double kPi = 3.14159265358979323846;
+
+// cos and sin of 2 pi k / n for integer k and n a power of two (n >= 8), reduced by exact
+// octant symmetry before the series.
+__host__ __device__ constexpr double ct_cos2pi(int k, int n)
+{
+    int m = ((k % n) + n) % n;
+    int q = (4 * m) / n;           // quadrant
+    int rem = m - q * (n / 4);     // 0 <= rem < n/4
+    bool flip = 8 * rem > n;       // past the octant: use the complementary angle
+    double th = 2.0 * kPi * double(flip ? (n / 4 - rem) : rem) / double(n);
+    double c = flip ? ct_sin_small(th) : ct_cos_small(th);
+    double s = flip ? ct_cos_small(th) : ct_sin_small(th);
+    // rotate (c, s) by q quarter turns
+    return q == 0 ? c : q == 1 ? -s : q == 2 ? -c : s;
+}
+__host__ __device__ constexpr double ct_sin2pi(int k, int n)
+{
+    int m = ((k % n) + n) % n;
+    int q = (4 * m) / n;
+    int rem = m - q * (n / 4);
+    bool flip = 8 * rem > n;
+    double th = 2.0 * kPi * double(flip ? (n / 4 - rem) : rem) / double(n);
+    double c = flip ? ct_sin_small(th) : ct_cos_small(th);
+    double s = flip ? ct_cos_small(th) : ct_sin_small(th);
+    return q == 0 ? s : q == 1 ? c : q == 2 ? -s : -c;
+}
+
+// ---------------------------------------------------------------- complex helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// z * exp(-2 pi i I / LEN) with the trivial factors special-cased.
+template <int I, int LEN>
+__device__ __forceinline__ float2 mul_w(float2 z)
+{
+    constexpr int i = ((I % LEN) + LEN) % LEN;
+    if constexpr (i == 0) {
+        return z;
+    } else if constexpr (4 * i == LEN) {          // -i
+        return make_float2(z.y, -z.x);
+    } else if constexpr (2 * i == LEN) {          // -1
+        return make_float2(-z.x, -z.y);
+    } else if constexpr (4 * i == 3 * LEN) {      // +i
+        return make_float2(-z.y, z.x);
+    } else if constexpr (8 * i == LEN) {          // (1 - i)/sqrt2
+        constexpr float r = 0.70710678118654752440f;
+        return make_float2((z.x + z.y) * r, (z.y - z.x) * r);
+    } else if constexpr (8 * i == 3 * LEN) {      // (-1 - i)/sqrt2
+        constexpr float r = 0.70710678118654752440f;
+        return make_float2((z.y - z.x) * r, -(z.x + z.y) * r);
+    } else {
+        constexpr float c = float(ct_cos2pi(i, LEN));
+        constexpr float s = float(ct_sin2pi(i, LEN));
+        // (x + iy)(c - is) = (xc + ys) + i(yc - xs)
+        return make_float2(fmaf(z.x, c, z.y * s), fmaf(z.y, c, -z.x * s));
+    }
+}
+
+// One decimation-in-frequency radix-2 stage of sub-length LEN over v[OFF .. OFF+R).
+template <int R, int LEN>
+__device__ __forceinline__ void dif_stage(float2* v)
+{
+    constexpr int H = LEN / 2;
+    static_for<R / LEN>([&](auto Sb) {
+        constexpr int s = decltype(Sb)::value * LEN;
+        static_for<H>([&](auto Iv) {
+            constexpr int i = decltype(Iv)::value;
+            float2 a = v[s + i], b = v[s + i + H];
+            v[s + i] = cadd(a, b);
+            v[s + i + H] = mul_w<i, LEN>(csub(a, b));
+        });
+    });
+    if constexpr (LEN > 2) dif_stage<R, LEN / 2>(v);
+}
+
+// In-place R-point forward DFT of v[0..R): afterwards V[q] = v[bitrev(q)].
+template <int R>
+__device__ __forceinline__ void dft(float2* v)
+{
+    if constexpr (R > 1) dif_stage<R, R>(v);
+}
+
+template <int R>
+struct BitRev {
+    static constexpr int bits = ilog2(R);
+    __host__ __device__ static constexpr int at(int q) { return bitrev(q, bits); }
+};
+
+}  // namespace isr

@@ -1,0 +1,398 @@
+// isr_kernel.cuh -- fused decode -> FFT -> |X|^2 integration kernel for sm_103a.
+//
+// One CTA (512 threads) owns G = 16384 / nfft range gates for one chunk of IPPs (for
+// nfft = 16384: one gate).  Per IPP and gate it
+//   1. waits for the gate's int16 IQ echo window, staged into shared memory by a bulk
+//      asynchronous copy (cp.async.bulk + mbarrier) that was issued one IPP ahead;
+//   2. decodes x[k] = conj(eps[k]) * m[s_r + k] on the fly while loading the first
+//      radix pass (Eq. 7 of the paper, the "complex multiplication" kernel of Sec. 3.2.1);
+//   3. runs a Stockham radix-32/16/8 FFT: each thread owns 32 points, every pass is a
+//      register-resident radix-R DFT, passes exchange data through a padded (bank-
+//      conflict-free) shared-memory buffer (the transform of Sec. 3.2.2);
+//   4. adds |X[f]|^2 into 32 FP32 accumulators per thread that stay in registers for the
+//      whole IPP chunk (Eq. 8, the "spectrum accumulation" kernel of Sec. 3.2.3).
+// At the end of the chunk each thread writes its 32 partial sums once; a separate
+// reduction adds the chunk partials into FP64 accumulators.
+#pragma once
+
+#include <cstdint>
+
+#include "isr_fft.cuh"
+
+namespace isr {
+
+enum TxKind { TX_CI16 = 0, TX_C32 = 1, TX_PM1 = 2 };
+
+constexpr int kThreads = 512;
+
+// ---------------------------------------------------------------- per-size schedule
+template <int LOG2N>
+struct Sched {
+    static constexpr int N = 1 << LOG2N;
+    static constexpr int E = N < 32 ? N : 32;   // points per thread
+    static constexpr int T = N / E;             // threads per transform
+    static constexpr int G = kThreads / T;      // transforms (gates) per CTA
+    // radices of the Stockham passes, first to last
+    static constexpr int NP = LOG2N <= 5 ? 1 : LOG2N <= 10 ? 2 : 3;
+    static constexpr int R0 = LOG2N == 3 ? 8 : LOG2N == 4 ? 16 : LOG2N == 5 ? 32
+                            : LOG2N == 6 ? 8 : LOG2N == 7 ? 16 : LOG2N == 8 ? 16
+                            : LOG2N == 9 ? 32 : LOG2N == 10 ? 32 : LOG2N == 11 ? 16
+                            : LOG2N == 12 ? 16 : 32;
+    static constexpr int R1 = LOG2N <= 5 ? 1 : LOG2N == 6 ? 8 : LOG2N == 7 ? 8 : LOG2N == 8 ? 16
+                            : LOG2N == 9 ? 16 : LOG2N == 10 ? 32 : LOG2N == 14 ? 32 : 16;
+    static constexpr int R2 = LOG2N <= 10 ? 1 : LOG2N == 11 ? 8 : 16;
+    static_assert(R0 * R1 * R2 == N, "radix product must equal nfft");
+    __host__ __device__ static constexpr int radix(int p) { return p == 0 ? R0 : p == 1 ? R1 : R2; }
+    // twiddle-base slots: one per (pass >= 1, butterfly of the thread)
+    static constexpr int NSLOT = (NP > 1 ? E / R1 : 0) + (NP > 2 ? E / R2 : 0);
+    // shared-memory exchange buffer: one pad element per PADP keeps every access pattern
+    // of the passes free of bank conflicts (stride R0 + 1 for the first pass' writes)
+    static constexpr int PADP = R0 < 16 ? 16 : R0;
+    static constexpr int NPAD = NP > 1 ? N + N / PADP : 0;
+    static constexpr int STAGE_WORDS = N + 4;   // window + alignment slack, 16-byte multiple
+    // dynamic shared-memory layout (bytes)
+    static constexpr int OFF_MBAR = 0;
+    static constexpr int OFF_TW = 16 * ((8 * G + 15) / 16);
+    static constexpr int OFF_STAGE = OFF_TW + 16 * ((8 * NSLOT * T + 15) / 16);
+    static constexpr int OFF_XCH = OFF_STAGE + 4 * STAGE_WORDS * G;
+    static constexpr int SMEM = OFF_XCH + 8 * NPAD * G;
+};
+
+__device__ __forceinline__ int pidx(int i, int padp) { return i + i / padp; }
+
+// u[k] = buf[padded(j + k * STRIDE)], k < R.  When STRIDE is a multiple of the pad period
+// the padded addresses are one base plus compile-time offsets.
+template <int STRIDE, int R, int PADP>
+__device__ __forceinline__ void load_strided(float2* u, const float2* buf, int j)
+{
+    if constexpr (STRIDE % PADP == 0) {
+        const float2* b = buf + pidx(j, PADP);
+        static_for<R>([&](auto Kc) {
+            constexpr int k = decltype(Kc)::value;
+            u[k] = b[k * (STRIDE + STRIDE / PADP)];
+        });
+    } else {
+        static_for<R>([&](auto Kc) {
+            constexpr int k = decltype(Kc)::value;
+            u[k] = buf[pidx(j + k * STRIDE, PADP)];
+        });
+    }
+}
+
+// buf[padded(base + q * STRIDE)] = X[q] = u[bitrev(q)], q < R (the DFT output order).
+// base is a multiple of R when STRIDE == 1 and R >= PADP or STRIDE is a multiple of PADP.
+template <int STRIDE, int R, int PADP>
+__device__ __forceinline__ void store_strided(float2* buf, int base, const float2* u)
+{
+    if constexpr ((STRIDE == 1 && R == PADP) || (STRIDE % PADP == 0)) {
+        float2* b = buf + pidx(base, PADP);
+        static_for<R>([&](auto Qc) {
+            constexpr int q = decltype(Qc)::value;
+            constexpr int o = STRIDE == 1 ? q : q * (STRIDE + STRIDE / PADP);
+            b[o] = u[BitRev<R>::at(q)];
+        });
+    } else {
+        static_for<R>([&](auto Qc) {
+            constexpr int q = decltype(Qc)::value;
+            buf[pidx(base + q * STRIDE, PADP)] = u[BitRev<R>::at(q)];
+        });
+    }
+}
+
+struct KArgs {
+    const uint32_t* echo;   // complex int16 samples as 32-bit words, 16-byte aligned
+    int64_t echo_stride;    // words per IPP row (multiple of 4)
+    const void* tx;         // code rows
+    int64_t tx_stride;      // chips between code rows (0 = shared)
+    float* partial;         // [n_chunks][n_ranges][N]
+    int* status;            // bit 0: a wait timed out
+    int n_ranges;
+    int range_start;
+    int range_step;
+    int code_len;
+    int n_ipp;              // IPPs in this launch (rows of echo)
+    int chunk_len;          // IPPs per chunk (blockIdx.y)
+    unsigned wait_limit;    // try_wait polls before giving up
+    int drop_ipp;           // test hook: never stage this IPP (launch-relative), -1 = off
+};
+
+// ---------------------------------------------------------------- async-copy primitives
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// arm the barrier for `bytes` and start one bulk global->shared copy completing on it
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// bounded wait for phase `parity` of the barrier; false if it did not complete in time
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned limit)
+{
+    for (unsigned i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------- decode helpers
+__device__ __forceinline__ float2 iq_of(uint32_t w)
+{
+    return make_float2((float)(int16_t)(w & 0xffffu), (float)(int16_t)(w >> 16));
+}
+
+template <int TXT>
+__device__ __forceinline__ float2 decode(uint32_t w, const void* txrow, int pos, uint32_t sbit)
+{
+    float2 m = iq_of(w);
+    if constexpr (TXT == TX_PM1) {
+        return sbit ? make_float2(-m.x, -m.y) : m;
+    } else if constexpr (TXT == TX_CI16) {
+        float2 e = iq_of(__ldg(reinterpret_cast<const uint32_t*>(txrow) + pos));
+        // conj(e) * m = (ex mx + ey my) + i (ex my - ey mx)
+        return make_float2(fmaf(e.x, m.x, e.y * m.y), fmaf(e.x, m.y, -e.y * m.x));
+    } else {
+        float2 e = __ldg(reinterpret_cast<const float2*>(txrow) + pos);
+        return make_float2(fmaf(e.x, m.x, e.y * m.y), fmaf(e.x, m.y, -e.y * m.x));
+    }
+}
+
+// sign bits of the code chips a thread decodes in the first pass (bit b*R0 + k)
+template <int LOG2N>
+__device__ __forceinline__ uint32_t load_signs(const int8_t* row, int t, int code_len)
+{
+    using S = Sched<LOG2N>;
+    uint32_t m = 0;
+    static_for<S::E / S::R0>([&](auto Bc) {
+        constexpr int b = decltype(Bc)::value;
+        static_for<S::R0>([&](auto Kc) {
+            constexpr int k = decltype(Kc)::value;
+            int pos = t + S::T * b + k * (S::N / S::R0);
+            if (pos < code_len && row[pos] < 0) m |= 1u << (b * S::R0 + k);
+        });
+    });
+    return m;
+}
+
+// apply the Stockham twiddles w^k (k = 1..R-1) to v[0..R) given w
+template <int R>
+__device__ __forceinline__ void twiddle(float2* v, float2 w)
+{
+    float2 cur = w;
+    static_for<R - 1>([&](auto Kc) {
+        constexpr int k = decltype(Kc)::value + 1;
+        v[k] = cmul(v[k], cur);
+        if constexpr (k + 1 < R) cur = cmul(cur, w);
+    });
+}
+
+// ---------------------------------------------------------------- the fused kernel
+template <int LOG2N, int TXT>
+__global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
+{
+    using S = Sched<LOG2N>;
+    constexpr int N = S::N, E = S::E, T = S::T, G = S::G, NP = S::NP;
+    constexpr int R0 = S::R0;
+    constexpr int RL = S::radix(NP - 1);  // radix of the last pass
+    // transforms of 32 or fewer threads live inside one warp and sync per warp
+    constexpr bool CTA_SYNC = T > 32;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
+    float2* twb = reinterpret_cast<float2*>(smem + S::OFF_TW);
+
+    const int tid = threadIdx.x;
+    const int g = tid / T;
+    const int t = tid - g * T;
+    const int r = blockIdx.x * G + g;
+    const bool valid = r < a.n_ranges;
+    const int64_t s_r = (int64_t)a.range_start + (int64_t)(valid ? r : a.n_ranges - 1) * a.range_step;
+    const int c = blockIdx.y;
+    const int p_begin = c * a.chunk_len;
+    const int p_end = min(p_begin + a.chunk_len, a.n_ipp);
+
+    uint32_t* stage = reinterpret_cast<uint32_t*>(smem + S::OFF_STAGE) + g * S::STAGE_WORDS;
+    float2* xch = reinterpret_cast<float2*>(smem + S::OFF_XCH) + g * S::NPAD;
+    const uint32_t bar = smem_u32(&mbar[g]);
+
+    // window geometry: the copy starts at the 16-byte boundary at or below s_r
+    const int off = (int)(s_r & 3);
+    const uint32_t copy_bytes = (uint32_t)(((off + a.code_len + 3) & ~3) * 4);
+    auto issue = [&](int p) {
+        const uint32_t* src = a.echo + (int64_t)p * a.echo_stride + (s_r - off);
+        bulk_load(smem_u32(stage), src, copy_bytes, bar);
+    };
+
+    if (t == 0) mbar_init(bar, 1);
+    // twiddle bases: w = exp(-2 pi i (j mod Ns) / (Ns R)) for each (pass >= 1, butterfly)
+    for (int i = tid; i < S::NSLOT * T; i += kThreads) {
+        int slot = i / T, tt = i - slot * T;
+        int pass = 1, b = slot, ns = R0;
+        if (NP > 2 && slot >= E / S::R1) {
+            pass = 2;
+            b = slot - E / S::R1;
+            ns = R0 * S::R1;
+        }
+        int R = S::radix(pass);
+        int j = tt + T * b;
+        double sn, cs;
+        sincospi(-2.0 * (double)(j % ns) / (double)(ns * R), &sn, &cs);
+        twb[i] = make_float2((float)cs, (float)sn);
+    }
+    fence_barrier_init();
+    __syncthreads();
+
+    if (t == 0 && p_begin < p_end && p_begin != a.drop_ipp) issue(p_begin);
+
+    const char* txbase = reinterpret_cast<const char*>(a.tx);
+    constexpr int CHIP = TXT == TX_CI16 ? 4 : TXT == TX_C32 ? 8 : 1;
+    uint32_t signs = 0;
+    if constexpr (TXT == TX_PM1) {
+        if (a.tx_stride == 0) signs = load_signs<LOG2N>(reinterpret_cast<const int8_t*>(txbase), t, a.code_len);
+    }
+
+    float acc[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) acc[i] = 0.f;
+
+    float2 v[E];
+    bool timed_out = false;
+    int it = 0;
+    for (int p = p_begin; p < p_end; ++p, ++it) {
+        const bool ok = mbar_wait(bar, (uint32_t)(it & 1), a.wait_limit);
+        // every thread of the CTA agrees before anyone leaves; this barrier also orders the
+        // previous IPP's last-pass reads of xch before this IPP's first-pass writes
+        const bool any_fail = CTA_SYNC ? __syncthreads_or(!ok) : __any_sync(0xffffffffu, !ok);
+        if (any_fail) {
+            timed_out = true;
+            break;
+        }
+        const char* txrow = txbase + (size_t)p * (size_t)a.tx_stride * CHIP;
+        if constexpr (TXT == TX_PM1) {
+            if (a.tx_stride != 0) signs = load_signs<LOG2N>(reinterpret_cast<const int8_t*>(txrow), t, a.code_len);
+        }
+
+        // ---- pass 0: decode from the staged window, radix-R0 DFT
+        static_for<E / R0>([&](auto Bc) {
+            constexpr int b = decltype(Bc)::value;
+            const int j = t + T * b;
+            float2* u = v + b * R0;
+            static_for<R0>([&](auto Kc) {
+                constexpr int k = decltype(Kc)::value;
+                const int pos = j + k * (N / R0);
+                // chips at or past code_len are the zero padding (and are never read)
+                u[k] = make_float2(0.f, 0.f);
+                if (pos < a.code_len) u[k] = decode<TXT>(stage[off + pos], txrow, pos, (signs >> (b * R0 + k)) & 1u);
+            });
+            dft<R0>(u);
+            if constexpr (NP == 1) {
+                static_for<R0>([&](auto Qc) {
+                    constexpr int q = decltype(Qc)::value;
+                    float2 X = u[BitRev<R0>::at(q)];
+                    acc[b * R0 + q] = fmaf(X.x, X.x, fmaf(X.y, X.y, acc[b * R0 + q]));
+                });
+            } else {
+                // Stockham output of the first pass (Ns = 1): y[j R0 + q]
+                store_strided<1, R0, S::PADP>(xch, j * R0, u);
+            }
+        });
+
+        // window fully consumed and first-pass outputs visible
+        if (CTA_SYNC) __syncthreads(); else __syncwarp();
+        if (t == 0 && p + 1 < p_end && p + 1 != a.drop_ipp) {
+            fence_proxy_async();
+            issue(p + 1);
+        }
+        if constexpr (NP == 1) continue;
+
+        // ---- middle pass (three-pass sizes): read all, barrier, write all
+        if constexpr (NP == 3) {
+            constexpr int R = S::R1, NS = R0;
+            static_for<E / R>([&](auto Bc) {
+                constexpr int b = decltype(Bc)::value;
+                const int j = t + T * b;
+                float2* u = v + b * R;
+                load_strided<N / R, R, S::PADP>(u, xch, j);
+                twiddle<R>(u, twb[b * T + t]);
+                dft<R>(u);
+            });
+            if (CTA_SYNC) __syncthreads(); else __syncwarp();
+            static_for<E / R>([&](auto Bc) {
+                constexpr int b = decltype(Bc)::value;
+                const int j = t + T * b;
+                const int idxD = (j / NS) * NS * R + (j % NS);
+                store_strided<NS, R, S::PADP>(xch, idxD, v + b * R);
+            });
+            if (CTA_SYNC) __syncthreads(); else __syncwarp();
+        }
+
+        // ---- last pass: read, twiddle, DFT, accumulate |X|^2 in registers
+        {
+            constexpr int R = RL;
+            constexpr int SLOT0 = NP == 3 ? E / S::R1 : 0;
+            static_for<E / R>([&](auto Bc) {
+                constexpr int b = decltype(Bc)::value;
+                const int j = t + T * b;
+                float2* u = v + b * R;
+                load_strided<N / R, R, S::PADP>(u, xch, j);
+                twiddle<R>(u, twb[(SLOT0 + b) * T + t]);
+                dft<R>(u);
+                static_for<R>([&](auto Qc) {
+                    constexpr int q = decltype(Qc)::value;
+                    float2 X = u[BitRev<R>::at(q)];
+                    acc[b * R + q] = fmaf(X.x, X.x, fmaf(X.y, X.y, acc[b * R + q]));
+                });
+            });
+        }
+    }
+
+    if (timed_out) {
+        if (tid == 0) atomicOr(a.status, 1);
+        // let the copy still in flight land before the CTA's shared memory is released
+        mbar_wait(bar, (uint32_t)(it & 1), a.wait_limit);
+        return;
+    }
+
+    // ---- chunk partials: bin of acc[b*RL + q] is j + q * N / RL, j = t + T b
+    if (valid) {
+        float* out = a.partial + ((int64_t)c * a.n_ranges + r) * N;
+        static_for<E / RL>([&](auto Bc) {
+            constexpr int b = decltype(Bc)::value;
+            const int j = t + T * b;
+            static_for<RL>([&](auto Qc) {
+                constexpr int q = decltype(Qc)::value;
+                out[j + q * (N / RL)] = acc[b * RL + q];
+            });
+        });
+    }
+}
+
+}  // namespace isr

@@ -1,0 +1,39 @@
+// isr_kernels.cuh -- kernel registry shared by the instantiation units and the host API.
+#pragma once
+
+#include "isr_kernel.cuh"
+
+namespace isr {
+
+struct KernelEntry {
+    const void* fn;   // __global__ integrate_kernel<LOG2N, TXT>
+    int smem;         // dynamic shared memory bytes
+    int gates;        // range gates per CTA (G)
+    int threads;      // threads per CTA
+};
+
+template <int L>
+KernelEntry entry_for(int txt)
+{
+    using S = Sched<L>;
+    const void* f = txt == TX_CI16 ? (const void*)integrate_kernel<L, TX_CI16>
+                  : txt == TX_C32  ? (const void*)integrate_kernel<L, TX_C32>
+                                   : (const void*)integrate_kernel<L, TX_PM1>;
+    return KernelEntry{f, S::SMEM, S::G, kThreads};
+}
+
+// defined in the instantiation units (one per group of sizes, compiled in parallel)
+KernelEntry entry_small(int log2n, int txt);  // nfft 8 .. 512
+KernelEntry entry_mid(int log2n, int txt);    // nfft 1024 .. 4096
+KernelEntry entry_8192(int txt);
+KernelEntry entry_16384(int txt);
+
+inline KernelEntry kernel_entry(int log2n, int txt)
+{
+    if (log2n <= 9) return entry_small(log2n, txt);
+    if (log2n <= 12) return entry_mid(log2n, txt);
+    if (log2n == 13) return entry_8192(txt);
+    return entry_16384(txt);
+}
+
+}  // namespace isr

@@ -1,0 +1,249 @@
+"""Thin ctypes binding of ``include/isr.h`` (argument marshalling only).
+
+Every computation happens in ``lib/libisr.so``; this module converts Python arguments
+(torch tensors, numpy arrays or raw integer addresses) into the C structs and pointers
+the library expects and turns non-zero status codes into ``IsrError``.  There is no
+fallback: if the library is missing the import of the binding fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libisr.so")
+
+ISR_OK = 0
+ISR_ERR_INVALID_ARG = 1
+ISR_ERR_UNSUPPORTED = 2
+ISR_ERR_OUT_OF_RANGE = 3
+ISR_ERR_NO_MEMORY = 4
+ISR_ERR_CUDA = 5
+ISR_ERR_TIMEOUT = 6
+
+ISR_TX_CI16 = 0
+ISR_TX_C32 = 1
+ISR_TX_PM1 = 2
+
+ISR_RESET_AFTER = 1
+ISR_MEAN = 2
+
+STATUS_NAMES = {0: "ISR_OK", 1: "ISR_ERR_INVALID_ARG", 2: "ISR_ERR_UNSUPPORTED", 3: "ISR_ERR_OUT_OF_RANGE",
+                4: "ISR_ERR_NO_MEMORY", 5: "ISR_ERR_CUDA", 6: "ISR_ERR_TIMEOUT"}
+
+# every entry point declared in include/isr.h
+EXPORTS = ("isr_plan_create", "isr_integrate", "isr_spectra", "isr_plan_query", "isr_plan_set_profiling",
+           "isr_plan_set_wait_limit", "isr_plan_test_drop_window", "isr_destroy", "isr_last_error")
+
+
+class IsrPlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("nfft", ctypes.c_int32),
+        ("code_len", ctypes.c_int32),
+        ("n_ranges", ctypes.c_int32),
+        ("range_start", ctypes.c_int32),
+        ("range_step", ctypes.c_int32),
+        ("tx_type", ctypes.c_int32),
+        ("echo_stride", ctypes.c_int64),
+        ("tx_stride", ctypes.c_int64),
+        ("ipp_chunk", ctypes.c_int32),
+        ("max_chunks", ctypes.c_int32),
+        ("device", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class IsrRanges(ctypes.Structure):
+    _fields_ = [("start", ctypes.c_int32), ("step", ctypes.c_int32), ("count", ctypes.c_int32)]
+
+
+class IsrPlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("nfft", ctypes.c_int32),
+        ("n_ranges", ctypes.c_int32),
+        ("ranges_per_cta", ctypes.c_int32),
+        ("threads_per_cta", ctypes.c_int32),
+        ("smem_bytes", ctypes.c_int32),
+        ("max_chunks", ctypes.c_int32),
+        ("ipp_chunk", ctypes.c_int32),
+        ("sm_count", ctypes.c_int32),
+        ("n_ipp_integrated", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
+        ("kernel_ms", ctypes.c_double),
+        ("kernel_timed", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class IsrError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libisr.so (built by ``__graft_entry__.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.isr_plan_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(IsrPlanDesc)]
+    lib.isr_integrate.argtypes = [P, P, P, ctypes.c_int32, ctypes.POINTER(IsrRanges), ctypes.c_int32]
+    lib.isr_spectra.argtypes = [P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+    lib.isr_plan_query.argtypes = [P, ctypes.POINTER(IsrPlanInfo)]
+    lib.isr_plan_set_profiling.argtypes = [P, ctypes.c_int32]
+    lib.isr_plan_set_wait_limit.argtypes = [P, ctypes.c_uint32]
+    lib.isr_plan_test_drop_window.argtypes = [P, ctypes.c_int32]
+    lib.isr_destroy.argtypes = [P]
+    lib.isr_destroy.restype = None
+    lib.isr_last_error.argtypes = []
+    lib.isr_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("isr_destroy", "isr_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != ISR_OK:
+        msg = load_library().isr_last_error().decode(errors="replace")
+        raise IsrError(status, where, msg)
+
+
+def _addr(x) -> int | None:
+    """Address of a torch tensor, numpy array or integer (None stays NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x).__name__}")
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+# ---------------------------------------------------------------- C-named entry points
+def isr_plan_create(desc: IsrPlanDesc) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().isr_plan_create(ctypes.byref(h), ctypes.byref(desc)), "isr_plan_create")
+    return h
+
+
+def isr_integrate(plan, echo, tx_code, n_ipp: int, ranges: IsrRanges | None, nfft: int) -> None:
+    _check(load_library().isr_integrate(plan, _addr(echo), _addr(tx_code), int(n_ipp),
+                                        None if ranges is None else ctypes.byref(ranges), int(nfft)),
+           "isr_integrate")
+
+
+def isr_spectra(plan, out, flags: int = 0) -> int:
+    n = ctypes.c_int64()
+    _check(load_library().isr_spectra(plan, _addr(out), int(flags), ctypes.byref(n)), "isr_spectra")
+    return n.value
+
+
+def isr_plan_query(plan) -> IsrPlanInfo:
+    info = IsrPlanInfo()
+    _check(load_library().isr_plan_query(plan, ctypes.byref(info)), "isr_plan_query")
+    return info
+
+
+def isr_plan_set_profiling(plan, enable: bool) -> None:
+    _check(load_library().isr_plan_set_profiling(plan, 1 if enable else 0), "isr_plan_set_profiling")
+
+
+def isr_plan_set_wait_limit(plan, polls: int) -> None:
+    _check(load_library().isr_plan_set_wait_limit(plan, int(polls)), "isr_plan_set_wait_limit")
+
+
+def isr_plan_test_drop_window(plan, ipp: int) -> None:
+    _check(load_library().isr_plan_test_drop_window(plan, int(ipp)), "isr_plan_test_drop_window")
+
+
+def isr_destroy(plan) -> None:
+    load_library().isr_destroy(plan)
+
+
+def isr_last_error() -> str:
+    return load_library().isr_last_error().decode(errors="replace")
+
+
+# ---------------------------------------------------------------- convenience wrapper
+class Plan:
+    """Owns one ``isr_plan``; ``integrate`` and ``spectra`` forward to the C calls."""
+
+    def __init__(self, *, nfft: int, n_ranges: int, echo_stride: int, code_len: int | None = None,
+                 range_start: int = 0, range_step: int = 25, tx_type: int = ISR_TX_PM1, tx_stride: int = 0,
+                 ipp_chunk: int = 0, max_chunks: int = 0, device: int = -1, stream=None):
+        d = IsrPlanDesc()
+        d.nfft = nfft
+        d.code_len = nfft if code_len is None else code_len
+        d.n_ranges = n_ranges
+        d.range_start = range_start
+        d.range_step = range_step
+        d.tx_type = tx_type
+        d.echo_stride = echo_stride
+        d.tx_stride = tx_stride
+        d.ipp_chunk = ipp_chunk
+        d.max_chunks = max_chunks
+        d.device = device
+        d.flags = 0
+        d.stream = _stream_handle(stream)
+        self.desc = d
+        self.handle = isr_plan_create(d)
+
+    def integrate(self, echo, tx_code, n_ipp: int, ranges: tuple[int, int] | None = None) -> None:
+        rg = None
+        if ranges is not None:
+            rg = IsrRanges(int(ranges[0]), int(ranges[1]), self.desc.n_ranges)
+        isr_integrate(self.handle, echo, tx_code, n_ipp, rg, self.desc.nfft)
+
+    def spectra(self, out=None, flags: int = 0):
+        """Copy the spectra into ``out`` (tensor/array, device or host) or a new CPU float32
+        torch tensor; returns (out, n_ipp_integrated)."""
+        if out is None:
+            import torch
+            out = torch.empty((self.desc.n_ranges, self.desc.nfft), dtype=torch.float32, pin_memory=False)
+        n = isr_spectra(self.handle, out, flags)
+        return out, n
+
+    def info(self) -> dict:
+        return isr_plan_query(self.handle).as_dict()
+
+    def set_profiling(self, enable: bool = True) -> None:
+        isr_plan_set_profiling(self.handle, enable)
+
+    def close(self) -> None:
+        if self.handle:
+            isr_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
