@@ -41,13 +41,26 @@ def _peaks():
         return {}
 
 
-def _workload(name, rank):
+def _workload(name, rank, n_ranges=None, n_ipp=None):
     import synth
+    kw = {}
+    if n_ranges:
+        kw["n_ranges"] = n_ranges
+    if n_ipp:
+        kw["n_ipp"] = n_ipp
     if name == "small":
-        return synth.small(seed=1 + 1000 * rank)
-    if name == "paper":
-        return synth.paper(seed=3 + 1000 * rank)
-    return synth.realistic(seed=2 + 1000 * rank)
+        w = synth.small(seed=1 + 1000 * rank, **kw)
+    elif name == "paper":
+        w = synth.paper(seed=3 + 1000 * rank, **kw)
+    else:
+        w = synth.realistic(seed=2 + 1000 * rank, **kw)
+    if n_ranges and name != "paper":
+        # minimal echo row for the gate count, rounded up to 128 samples
+        need = w.range_start + (w.n_ranges - 1) * w.range_step + w.code_len
+        w.echo_stride = (need + 127) // 128 * 128
+    if n_ranges or n_ipp:
+        w.name += " (resized)"
+    return w
 
 
 def _workload_desc(w):
@@ -145,7 +158,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     threads = os.cpu_count() or 1
-    w = _workload(args.workload, 0)
+    w = _workload(args.workload, 0, args.n_ranges, args.n_ipp)
     gates, ipps = args.ref_gates, args.ref_ipps
     for _ in range(args.warmup):
         _cpu_sample(w, gates, ipps, threads)
@@ -182,7 +195,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    w = _workload(args.workload, rank)
+    w = _workload(args.workload, rank, args.n_ranges, args.n_ipp)
     R, N, P = w.n_ranges, w.nfft, w.n_ipp
     echo = torch.empty((P, w.echo_stride, 2), dtype=torch.int16, device=dev)
     code_d = torch.from_numpy(w.code()).to(dev)
@@ -327,8 +340,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-gates", type=int, default=64)
-    ap.add_argument("--ref-ipps", type=int, default=64)
+    ap.add_argument("--ref-gates", type=int, default=256)
+    ap.add_argument("--ref-ipps", type=int, default=256)
+    ap.add_argument("--n-ranges", type=int, default=None, help="resize the workload (profiling cases)")
+    ap.add_argument("--n-ipp", type=int, default=None, help="resize the workload (profiling cases)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -238,7 +238,7 @@ def _round_up(x: int, m: int) -> int:
 
 
 def small(seed: int = 1, **kw) -> Workload:
-    R, N, step = 64, 1024, 25
+    R, N, step = kw.get("n_ranges", 64), 1024, 25
     stride = _round_up((R - 1) * step + N, 128)
     base = dict(name="small", n_ranges=R, nfft=N, code_len=N, n_ipp=100, range_start=0,
                 range_step=step, echo_stride=stride, seed=seed, kind=TONE, snr_db=-10.0)
@@ -247,7 +247,7 @@ def small(seed: int = 1, **kw) -> Workload:
 
 
 def realistic(seed: int = 2, **kw) -> Workload:
-    R, N, step = 1000, 16384, 25
+    R, N, step = kw.get("n_ranges", 1000), 16384, 25
     stride = _round_up((R - 1) * step + N, 128)
     base = dict(name="realistic", n_ranges=R, nfft=N, code_len=N, n_ipp=10000, range_start=0,
                 range_step=step, echo_stride=stride, seed=seed, kind=LINE, snr_db=-20.0)
@@ -257,7 +257,6 @@ def realistic(seed: int = 2, **kw) -> Workload:
 
 def paper(seed: int = 3, **kw) -> Workload:
     base = dict(name="paper", n_ranges=4096, nfft=16384, code_len=16384, n_ipp=100, range_start=0,
-                range_step=25, echo_stride=250000 if (4095 * 25 + 16384) <= 250000 else 0,
-                seed=seed, kind=TONE, snr_db=-10.0)
+                range_step=25, echo_stride=250000, seed=seed, kind=TONE, snr_db=-10.0)
     base.update(kw)
     return Workload(**base)
