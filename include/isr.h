@@ -145,6 +145,30 @@ isr_status isr_plan_set_wait_limit(isr_plan* plan, uint32_t polls);
  * runs out and exercises the timeout path above without any fault. */
 isr_status isr_plan_test_drop_window(isr_plan* plan, int32_t ipp);
 
+/*
+ * Allocation-free integration (the paper has no counterpart; this serves callers that
+ * cannot allocate device memory, for example a real-time pipeline that reserves all of
+ * its GPU memory at start-up, or a process whose device memory belongs to another
+ * allocator such as a framework's caching allocator, where a cudaMalloc could fail or
+ * stall).  It computes, for the geometry in *desc, the sum over n_ipp IPPs of the same
+ * power spectra as a plan would (Eqs. 7-8), writing float [n_ranges][nfft] to `out`.
+ * echo, tx_code and out are caller-owned DEVICE buffers (echo 16-byte aligned); desc's
+ * ipp_chunk and max_chunks are ignored.  The IPP-chunk partial sums live in one
+ * file-scope device array of ISR_STATIC_SCRATCH_FLOATS floats (16 MiB) that every GPU
+ * which loads this library keeps until the process exits; n_ranges * nfft must not
+ * exceed it (ISR_ERR_INVALID_ARG otherwise).  Nothing is allocated: no cudaMalloc, no
+ * cudaFree, no allocating library routine.  The first call on a device looks up the
+ * array's device address (once per device, with that device current), so make that
+ * first call before any stream capture.  Every call shares the array and its contents
+ * stay from the last call: calls that overlap on the GPU (other host threads or other
+ * streams) race and corrupt each other's results.  The call is stream-ordered on
+ * desc->stream and returns after that stream has finished the work (so it can report
+ * ISR_ERR_TIMEOUT from a bounded wait that ran out).
+ */
+#define ISR_STATIC_SCRATCH_FLOATS (4 * 1024 * 1024)
+isr_status isr_integrate_static(const isr_plan_desc* desc, const int16_t* echo, const void* tx_code,
+                                int32_t n_ipp, float* out);
+
 /* Release the plan and its device memory (synchronises its stream first); NULL is safe. */
 void isr_destroy(isr_plan* plan);
 

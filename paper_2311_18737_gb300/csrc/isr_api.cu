@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -485,6 +486,147 @@ isr_status isr_plan_test_drop_window(isr_plan* p, int32_t ipp)
 {
     if (!p || ipp < -1) return fail(ISR_ERR_INVALID_ARG, "plan is NULL or ipp < -1");
     p->drop_ipp = ipp;
+    return ISR_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free variant
+namespace {
+
+// IPP-chunk partials of isr_integrate_static: [chunks][n_ranges][nfft] floats, plus the
+// variant's own status word.  Host code must not use these names as addresses (they are
+// host-side shadows); it looks up each device's copy with cudaGetSymbolAddress.
+__device__ __align__(256) float g_static_scratch[ISR_STATIC_SCRATCH_FLOATS];
+__device__ __align__(16) int g_static_status[4];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+float* g_static_scratch_ptr[kMaxDevices] = {};
+int* g_static_status_ptr[kMaxDevices] = {};
+
+// out[i] = (float) sum_c part[c][i], summed in double
+__global__ void reduce_to_spectra_kernel(const float* __restrict__ part, int n_chunks, int64_t n,
+                                         float* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0;
+        for (int c = 0; c < n_chunks; ++c) s += part[(int64_t)c * n + i];
+        out[i] = (float)s;
+    }
+}
+
+// device addresses of the file-scope arrays on `dev` (looked up once per device)
+isr_status static_buffers(int dev, float** scratch, int** status)
+{
+    if (dev < 0 || dev >= kMaxDevices) return fail(ISR_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_scratch_ptr[dev]) {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&a, g_static_scratch);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&b, g_static_status);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ISR_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        }
+        g_static_scratch_ptr[dev] = static_cast<float*>(a);
+        g_static_status_ptr[dev] = static_cast<int*>(b);
+    }
+    *scratch = g_static_scratch_ptr[dev];
+    *status = g_static_status_ptr[dev];
+    return ISR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+isr_status isr_integrate_static(const isr_plan_desc* desc, const int16_t* echo, const void* tx, int32_t n_ipp,
+                                float* out)
+{
+    g_err[0] = 0;
+    if (!desc) return fail(ISR_ERR_INVALID_ARG, "desc is NULL");
+    const isr_plan_desc& d = *desc;
+    if (d.nfft < 8 || d.nfft > 16384 || (d.nfft & (d.nfft - 1)))
+        return fail(ISR_ERR_UNSUPPORTED, "nfft %d is not a power of two in [8, 16384]", d.nfft);
+    if (d.tx_type != ISR_TX_CI16 && d.tx_type != ISR_TX_C32 && d.tx_type != ISR_TX_PM1)
+        return fail(ISR_ERR_UNSUPPORTED, "unknown tx_type %d", d.tx_type);
+    if (d.code_len < 1 || d.code_len > d.nfft) return fail(ISR_ERR_INVALID_ARG, "code_len must be in [1, nfft]");
+    if (d.n_ranges < 1) return fail(ISR_ERR_INVALID_ARG, "n_ranges must be >= 1");
+    if (d.echo_stride < 4 || d.echo_stride % 4) return fail(ISR_ERR_INVALID_ARG, "echo_stride must be a positive multiple of 4");
+    if (d.tx_stride < 0 || (d.tx_stride > 0 && d.tx_stride < d.code_len))
+        return fail(ISR_ERR_INVALID_ARG, "tx_stride must be 0 or >= code_len");
+    if (d.range_start > (1 << 30) || d.range_step > (1 << 30) || d.flags != 0)
+        return fail(ISR_ERR_INVALID_ARG, "range_start and range_step must be < 2^30, flags 0");
+    isr_status st = check_geometry(d, d.range_start, d.range_step);
+    if (st != ISR_OK) return st;
+    const int64_t RN = (int64_t)d.n_ranges * d.nfft;
+    if (RN > ISR_STATIC_SCRATCH_FLOATS)
+        return fail(ISR_ERR_INVALID_ARG, "n_ranges * nfft = %lld exceeds the static scratch of %d floats",
+                    (long long)RN, ISR_STATIC_SCRATCH_FLOATS);
+    if (n_ipp < 1) return fail(ISR_ERR_INVALID_ARG, "n_ipp must be >= 1");
+    if (!echo || !tx || !out) return fail(ISR_ERR_INVALID_ARG, "echo, tx_code and out must not be NULL");
+    if (reinterpret_cast<uintptr_t>(echo) % 16) return fail(ISR_ERR_INVALID_ARG, "echo must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(tx) % chip_bytes(d.tx_type))
+        return fail(ISR_ERR_INVALID_ARG, "tx_code must be aligned to its chip size");
+    if (!is_device_ptr(echo) || !is_device_ptr(tx) || !is_device_ptr(out))
+        return fail(ISR_ERR_INVALID_ARG, "echo, tx_code and out must be device memory");
+
+    int dev = d.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(ISR_ERR_CUDA, "no current CUDA device");
+    DeviceGuard guard(dev);
+    if (!guard.ok) return fail(ISR_ERR_CUDA, "cannot select CUDA device %d", dev);
+    float* scratch = nullptr;
+    int* status = nullptr;
+    st = static_buffers(dev, &scratch, &status);
+    if (st != ISR_OK) return st;
+
+    int lg = 0;
+    while ((1 << lg) < d.nfft) ++lg;
+    isr::KernelEntry ke = isr::kernel_entry(lg, d.tx_type);
+    CUDA_TRY(cudaFuncSetAttribute(ke.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ke.smem));
+    int sm_count = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t stream = static_cast<cudaStream_t>(d.stream);
+
+    // chunks: FP32 sums of at most kDefaultChunk IPPs while the scratch allows, two waves of
+    // CTAs when the IPP count allows, never more chunks than fit in the scratch
+    const int rg = (d.n_ranges + ke.gates - 1) / ke.gates;
+    const int64_t c_cap = std::min<int64_t>(65535, ISR_STATIC_SCRATCH_FLOATS / RN);
+    int64_t c_min = (n_ipp + kDefaultChunk - 1) / kDefaultChunk;
+    int64_t c_fill = (2 * (int64_t)sm_count + rg - 1) / rg;
+    int64_t C = std::min(c_cap, std::max(c_min, std::min<int64_t>(c_fill, n_ipp)));
+    int64_t chunk = (n_ipp + C - 1) / C;
+    C = (n_ipp + chunk - 1) / chunk;
+
+    CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), stream));
+    isr::KArgs a;
+    a.echo = reinterpret_cast<const uint32_t*>(echo);
+    a.echo_stride = d.echo_stride;
+    a.tx = tx;
+    a.tx_stride = d.tx_stride;
+    a.partial = scratch;
+    a.status = status;
+    a.n_ranges = d.n_ranges;
+    a.range_start = d.range_start;
+    a.range_step = d.range_step;
+    a.code_len = d.code_len;
+    a.n_ipp = n_ipp;
+    a.chunk_len = (int)chunk;
+    a.wait_limit = kDefaultWaitLimit;
+    a.drop_ipp = -1;
+    void* args[] = {&a};
+    CUDA_TRY(cudaLaunchKernel(ke.fn, dim3((unsigned)rg, (unsigned)C), dim3((unsigned)ke.threads), args,
+                              (size_t)ke.smem, stream));
+    int threads = 256;
+    int64_t blocks = std::min<int64_t>((RN + threads - 1) / threads, (int64_t)sm_count * 8);
+    reduce_to_spectra_kernel<<<(unsigned)blocks, threads, 0, stream>>>(scratch, (int)C, RN, out);
+    CUDA_TRY(cudaGetLastError());
+    int flag = 0;
+    CUDA_TRY(cudaMemcpyAsync(&flag, status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    if (flag) return fail(ISR_ERR_TIMEOUT, "a kernel timed out waiting for its staged echo window");
     return ISR_OK;
 }
 

@@ -33,7 +33,11 @@ STATUS_NAMES = {0: "ISR_OK", 1: "ISR_ERR_INVALID_ARG", 2: "ISR_ERR_UNSUPPORTED",
 
 # every entry point declared in include/isr.h
 EXPORTS = ("isr_plan_create", "isr_integrate", "isr_spectra", "isr_plan_query", "isr_plan_set_profiling",
-           "isr_plan_set_wait_limit", "isr_plan_test_drop_window", "isr_destroy", "isr_last_error")
+           "isr_plan_set_wait_limit", "isr_plan_test_drop_window", "isr_destroy", "isr_last_error",
+           "isr_integrate_static")
+
+# floats of the allocation-free variant's file-scope scratch array
+ISR_STATIC_SCRATCH_FLOATS = 4 * 1024 * 1024
 
 
 class IsrPlanDesc(ctypes.Structure):
@@ -103,6 +107,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isr_plan_set_profiling.argtypes = [P, ctypes.c_int32]
     lib.isr_plan_set_wait_limit.argtypes = [P, ctypes.c_uint32]
     lib.isr_plan_test_drop_window.argtypes = [P, ctypes.c_int32]
+    lib.isr_integrate_static.argtypes = [ctypes.POINTER(IsrPlanDesc), P, P, ctypes.c_int32, P]
     lib.isr_destroy.argtypes = [P]
     lib.isr_destroy.restype = None
     lib.isr_last_error.argtypes = []
@@ -176,6 +181,17 @@ def isr_plan_set_wait_limit(plan, polls: int) -> None:
 
 def isr_plan_test_drop_window(plan, ipp: int) -> None:
     _check(load_library().isr_plan_test_drop_window(plan, int(ipp)), "isr_plan_test_drop_window")
+
+
+def isr_integrate_static(desc: IsrPlanDesc, echo, tx_code, n_ipp: int, out) -> None:
+    """Allocation-free integration into ``out`` (device buffers only; synchronous).
+
+    For callers that cannot allocate device memory: the chunk partials live in a fixed
+    16 MiB device array inside the library, shared by every call, so calls must not
+    overlap on the GPU.  The first call on a device should come before any stream capture.
+    """
+    _check(load_library().isr_integrate_static(ctypes.byref(desc), _addr(echo), _addr(tx_code), int(n_ipp),
+                                               _addr(out)), "isr_integrate_static")
 
 
 def isr_destroy(plan) -> None:
