@@ -169,6 +169,22 @@ isr_status isr_plan_test_drop_window(isr_plan* plan, int32_t ipp);
 isr_status isr_integrate_static(const isr_plan_desc* desc, const int16_t* echo, const void* tx_code,
                                 int32_t n_ipp, float* out);
 
+/*
+ * Plasma-line position per gate by spectral peak fit (the line frequency gives the
+ * electron density through Eq. 1).  spectra: device float [n_ranges][nfft] (a sum or
+ * mean from isr_spectra).  For each gate r, within bins [band_lo, band_hi):
+ *   b      = the largest bin (lowest index on ties, compared in float),
+ *   delta  = 0.5 (y[b-1] - y[b+1]) / (y[b-1] - 2 y[b] + y[b+1]) with y = ln P in double
+ *            (neighbours taken modulo nfft; 0 unless the parabola opens downwards and all
+ *            three powers are positive; clamped to [-0.5, 0.5]),
+ *   freq_bin[r] = b + delta   (double; Hz = freq_bin * fs / nfft, negative frequencies
+ *                              are bins above nfft/2),
+ *   snr[r]      = P[b] / mean of P over the band (float).
+ * freq_bin and snr are device arrays of n_ranges.  Stream-ordered on `stream`, asynchronous.
+ */
+isr_status isr_peak_fit(const float* spectra, int32_t n_ranges, int32_t nfft, int32_t band_lo, int32_t band_hi,
+                        double* freq_bin, float* snr, void* stream);
+
 /* Release the plan and its device memory (synchronises its stream first); NULL is safe. */
 void isr_destroy(isr_plan* plan);
 

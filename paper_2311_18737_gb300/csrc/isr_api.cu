@@ -19,9 +19,10 @@
 #include "isr_kernels.cuh"
 
 namespace {
-
 thread_local char g_err[512] = "";
+}  // namespace
 
+namespace isr {
 isr_status fail(isr_status st, const char* fmt, ...)
 {
     va_list ap;
@@ -30,6 +31,11 @@ isr_status fail(isr_status st, const char* fmt, ...)
     va_end(ap);
     return st;
 }
+void clear_error() { g_err[0] = 0; }
+}  // namespace isr
+
+namespace {
+using isr::fail;
 
 #define CUDA_TRY(expr)                                                                   \
     do {                                                                                 \

@@ -43,8 +43,17 @@ struct Sched {
     static constexpr int R2 = LOG2N <= 10 ? 1 : LOG2N == 11 ? 8 : 16;
     static_assert(R0 * R1 * R2 == N, "radix product must equal nfft");
     __host__ __device__ static constexpr int radix(int p) { return p == 0 ? R0 : p == 1 ? R1 : R2; }
-    // twiddle-base slots: one per (pass >= 1, butterfly of the thread)
-    static constexpr int NSLOT = (NP > 1 ? E / R1 : 0) + (NP > 2 ? E / R2 : 0);
+    // Twiddles of pass p >= 1: w^k with w = exp(-2 pi i (j mod Ns) / (Ns R)).  A pass whose
+    // distinct values fit a small table (Ns (R - 1) <= 1024) reads them from a per-CTA
+    // table laid out [k - 1][j mod Ns] (consecutive lanes, consecutive entries); other
+    // passes build w^k by recurrence from a per-thread base w kept in a slot table.
+    __host__ __device__ static constexpr int ns(int p) { return p == 1 ? R0 : R0 * R1; }
+    __host__ __device__ static constexpr bool tab(int p) { return ns(p) * (radix(p) - 1) <= 1024; }
+    static constexpr int TAB1 = (NP > 1 && tab(1)) ? ns(1) * (R1 - 1) : 0;   // entries
+    static constexpr int TAB2 = (NP > 2 && tab(2)) ? ns(2) * (R2 - 1) : 0;
+    static constexpr int SLOTS1 = (NP > 1 && !tab(1)) ? E / R1 : 0;           // per-thread bases
+    static constexpr int SLOTS2 = (NP > 2 && !tab(2)) ? E / R2 : 0;
+    static constexpr int NSLOT = SLOTS1 + SLOTS2;
     // shared-memory exchange buffer: one pad element per PADP keeps every access pattern
     // of the passes free of bank conflicts (stride R0 + 1 for the first pass' writes)
     static constexpr int PADP = R0 < 16 ? 16 : R0;
@@ -53,7 +62,8 @@ struct Sched {
     // dynamic shared-memory layout (bytes)
     static constexpr int OFF_MBAR = 0;
     static constexpr int OFF_TW = 16 * ((8 * G + 15) / 16);
-    static constexpr int OFF_STAGE = OFF_TW + 16 * ((8 * NSLOT * T + 15) / 16);
+    static constexpr int OFF_TAB = OFF_TW + 16 * ((8 * NSLOT * T + 15) / 16);
+    static constexpr int OFF_STAGE = OFF_TAB + 16 * ((8 * (TAB1 + TAB2) + 15) / 16);
     static constexpr int OFF_XCH = OFF_STAGE + 4 * STAGE_WORDS * G;
     static constexpr int SMEM = OFF_XCH + 8 * NPAD * G;
 };
@@ -175,7 +185,8 @@ __device__ __forceinline__ float2 decode(uint32_t w, const void* txrow, int pos,
 {
     float2 m = iq_of(w);
     if constexpr (TXT == TX_PM1) {
-        return sbit ? make_float2(-m.x, -m.y) : m;
+        // sbit holds the chip's sign in bit 31: flip both components' sign bits
+        return make_float2(__int_as_float(__float_as_int(m.x) ^ sbit), __int_as_float(__float_as_int(m.y) ^ sbit));
     } else if constexpr (TXT == TX_CI16) {
         float2 e = iq_of(__ldg(reinterpret_cast<const uint32_t*>(txrow) + pos));
         // conj(e) * m = (ex mx + ey my) + i (ex my - ey mx)
@@ -215,6 +226,17 @@ __device__ __forceinline__ void twiddle(float2* v, float2 w)
     });
 }
 
+// apply w^k = tab[(k - 1) * NS + jm] (k = 1..R-1) to v[0..R)
+template <int R, int NS>
+__device__ __forceinline__ void twiddle_tab(float2* v, const float2* tab, int jm)
+{
+    const float2* t = tab + jm;
+    static_for<R - 1>([&](auto Kc) {
+        constexpr int k = decltype(Kc)::value + 1;
+        v[k] = cmul(v[k], t[(k - 1) * NS]);
+    });
+}
+
 // ---------------------------------------------------------------- the fused kernel
 template <int LOG2N, int TXT>
 __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
@@ -228,6 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
     float2* twb = reinterpret_cast<float2*>(smem + S::OFF_TW);
+    float2* tab = reinterpret_cast<float2*>(smem + S::OFF_TAB);
 
     const int tid = threadIdx.x;
     const int g = tid / T;
@@ -252,20 +275,26 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
     };
 
     if (t == 0) mbar_init(bar, 1);
-    // twiddle bases: w = exp(-2 pi i (j mod Ns) / (Ns R)) for each (pass >= 1, butterfly)
+    // per-thread twiddle bases of the recurrence passes, slot-major: [slot][t]
     for (int i = tid; i < S::NSLOT * T; i += kThreads) {
         int slot = i / T, tt = i - slot * T;
-        int pass = 1, b = slot, ns = R0;
-        if (NP > 2 && slot >= E / S::R1) {
-            pass = 2;
-            b = slot - E / S::R1;
-            ns = R0 * S::R1;
-        }
-        int R = S::radix(pass);
+        int pass = slot < S::SLOTS1 ? 1 : 2;
+        int b = pass == 1 ? slot : slot - S::SLOTS1;
+        int ns = S::ns(pass), R = S::radix(pass);
         int j = tt + T * b;
         double sn, cs;
         sincospi(-2.0 * (double)(j % ns) / (double)(ns * R), &sn, &cs);
         twb[i] = make_float2((float)cs, (float)sn);
+    }
+    // twiddle tables of the small passes: [k - 1][jm] = exp(-2 pi i jm k / (Ns R))
+    for (int i = tid; i < S::TAB1 + S::TAB2; i += kThreads) {
+        int pass = i < S::TAB1 ? 1 : 2;
+        int e = pass == 1 ? i : i - S::TAB1;
+        int ns = S::ns(pass), R = S::radix(pass);
+        int k = e / ns + 1, jm = e - (k - 1) * ns;
+        double sn, cs;
+        sincospi(-2.0 * (double)(jm * k) / (double)(ns * R), &sn, &cs);
+        tab[i] = make_float2((float)cs, (float)sn);
     }
     fence_barrier_init();
     __syncthreads();
@@ -310,7 +339,8 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
                 const int pos = j + k * (N / R0);
                 // chips at or past code_len are the zero padding (and are never read)
                 u[k] = make_float2(0.f, 0.f);
-                if (pos < a.code_len) u[k] = decode<TXT>(stage[off + pos], txrow, pos, (signs >> (b * R0 + k)) & 1u);
+                if (pos < a.code_len)
+                    u[k] = decode<TXT>(stage[off + pos], txrow, pos, (signs << (31 - (b * R0 + k))) & 0x80000000u);
             });
             dft<R0>(u);
             if constexpr (NP == 1) {
@@ -341,7 +371,8 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
                 const int j = t + T * b;
                 float2* u = v + b * R;
                 load_strided<N / R, R, S::PADP>(u, xch, j);
-                twiddle<R>(u, twb[b * T + t]);
+                if constexpr (S::tab(1)) twiddle_tab<R, NS>(u, tab, j % NS);
+                else twiddle<R>(u, twb[b * T + t]);
                 dft<R>(u);
             });
             if (CTA_SYNC) __syncthreads(); else __syncwarp();
@@ -357,13 +388,16 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
         // ---- last pass: read, twiddle, DFT, accumulate |X|^2 in registers
         {
             constexpr int R = RL;
-            constexpr int SLOT0 = NP == 3 ? E / S::R1 : 0;
+            constexpr int PL = NP - 1;                        // index of the last pass
+            constexpr int SLOT0 = PL == 2 ? S::SLOTS1 : 0;
+            constexpr int TAB0 = PL == 2 ? S::TAB1 : 0;
             static_for<E / R>([&](auto Bc) {
                 constexpr int b = decltype(Bc)::value;
                 const int j = t + T * b;
                 float2* u = v + b * R;
                 load_strided<N / R, R, S::PADP>(u, xch, j);
-                twiddle<R>(u, twb[(SLOT0 + b) * T + t]);
+                if constexpr (S::tab(PL)) twiddle_tab<R, S::ns(PL)>(u, tab + TAB0, j % S::ns(PL));
+                else twiddle<R>(u, twb[(SLOT0 + b) * T + t]);
                 dft<R>(u);
                 static_for<R>([&](auto Qc) {
                     constexpr int q = decltype(Qc)::value;

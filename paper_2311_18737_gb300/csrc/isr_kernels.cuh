@@ -1,9 +1,14 @@
 // isr_kernels.cuh -- kernel registry shared by the instantiation units and the host API.
 #pragma once
 
+#include "isr.h"
 #include "isr_kernel.cuh"
 
 namespace isr {
+
+// record a one-line reason for isr_last_error() and return st (defined in isr_api.cu)
+isr_status fail(isr_status st, const char* fmt, ...);
+void clear_error();
 
 struct KernelEntry {
     const void* fn;   // __global__ integrate_kernel<LOG2N, TXT>

@@ -34,7 +34,7 @@ STATUS_NAMES = {0: "ISR_OK", 1: "ISR_ERR_INVALID_ARG", 2: "ISR_ERR_UNSUPPORTED",
 # every entry point declared in include/isr.h
 EXPORTS = ("isr_plan_create", "isr_integrate", "isr_spectra", "isr_plan_query", "isr_plan_set_profiling",
            "isr_plan_set_wait_limit", "isr_plan_test_drop_window", "isr_destroy", "isr_last_error",
-           "isr_integrate_static")
+           "isr_integrate_static", "isr_peak_fit")
 
 # floats of the allocation-free variant's file-scope scratch array
 ISR_STATIC_SCRATCH_FLOATS = 4 * 1024 * 1024
@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isr_plan_set_wait_limit.argtypes = [P, ctypes.c_uint32]
     lib.isr_plan_test_drop_window.argtypes = [P, ctypes.c_int32]
     lib.isr_integrate_static.argtypes = [ctypes.POINTER(IsrPlanDesc), P, P, ctypes.c_int32, P]
+    lib.isr_peak_fit.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P]
     lib.isr_destroy.argtypes = [P]
     lib.isr_destroy.restype = None
     lib.isr_last_error.argtypes = []
@@ -192,6 +193,12 @@ def isr_integrate_static(desc: IsrPlanDesc, echo, tx_code, n_ipp: int, out) -> N
     """
     _check(load_library().isr_integrate_static(ctypes.byref(desc), _addr(echo), _addr(tx_code), int(n_ipp),
                                                _addr(out)), "isr_integrate_static")
+
+
+def isr_peak_fit(spectra, n_ranges: int, nfft: int, band_lo: int, band_hi: int, freq_bin, snr,
+                 stream=None) -> None:
+    _check(load_library().isr_peak_fit(_addr(spectra), int(n_ranges), int(nfft), int(band_lo), int(band_hi),
+                                       _addr(freq_bin), _addr(snr), _stream_handle(stream)), "isr_peak_fit")
 
 
 def isr_destroy(plan) -> None:

@@ -1,0 +1,63 @@
+"""Pins of the FP64 estimator reference: its hand-written backward pass equals central
+finite differences of its forward loss; features are standardised; the soft-argmax
+prediction of a sharp logit map lands on the logit peak."""
+import numpy as np
+
+from oracle import estimator as est
+
+
+def _case(seed, B=3, L=40):
+    rng = np.random.default_rng(seed)
+    theta = est.init_params(seed) + 0.05 * rng.standard_normal(est.N_PARAMS)
+    x = rng.standard_normal((B, L))
+    f = rng.uniform(3, L - 3, B)
+    y = np.array([1.0, 0.0, 1.0])[:B]
+    return theta, x, f, y
+
+
+def test_backward_matches_finite_differences():
+    theta, x, f, y = _case(1)
+    L0, g = est.loss_and_grad(theta, x, f, y)
+    assert abs(L0 - est.loss(theta, x, f, y)) < 1e-12
+    rng = np.random.default_rng(2)
+    idx = np.concatenate([rng.choice(est.N_PARAMS, 60, replace=False),
+                          np.arange(est.N_PARAMS - 2200, est.N_PARAMS)[::97]])
+    eps = 1e-6
+    for i in idx:
+        tp = theta.copy(); tp[i] += eps
+        tm = theta.copy(); tm[i] -= eps
+        num = (est.loss(tp, x, f, y) - est.loss(tm, x, f, y)) / (2 * eps)
+        assert abs(num - g[i]) <= 1e-6 + 1e-5 * abs(num), (i, num, g[i])
+
+
+def test_every_block_has_a_gradient():
+    theta, x, f, y = _case(3)
+    _, g = est.loss_and_grad(theta, x, f, y)
+    d = est.unpack(g)
+    for name, _ in est.SHAPES:
+        assert np.abs(d[name]).sum() > 0, name
+
+
+def test_features_standardised():
+    rng = np.random.default_rng(4)
+    P = rng.gamma(20, 1.0, size=(5, 300))
+    x = est.features(P, 10, 256)
+    assert np.allclose(x.mean(axis=1), 0, atol=1e-12)
+    assert np.allclose(x.std(axis=1), 1, atol=1e-4)
+
+
+def test_prediction_of_sharp_logits():
+    theta = np.zeros(est.N_PARAMS)
+    d = est.unpack(theta)
+    d["b1"][:] = 0.0
+    # identity-like path: channel 0 passes x through 4 layers, w5 reads it
+    for l in range(1, 5):
+        W = np.zeros_like(d[f"W{l}"])
+        W[0, 0, est.HALF] = 1.0
+        d[f"W{l}"] = W
+    d["w5"][0] = 50.0
+    theta = est.pack(d)
+    x = np.zeros((1, 64))
+    x[0, 20] = 1.0
+    pos, pres = est.predict(theta, x)
+    assert abs(pos[0] - 20.0) < 1e-9 and abs(pres[0] - 0.5) < 1e-12
