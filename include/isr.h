@@ -185,6 +185,44 @@ isr_status isr_integrate_static(const isr_plan_desc* desc, const int16_t* echo, 
 isr_status isr_peak_fit(const float* spectra, int32_t n_ranges, int32_t nfft, int32_t band_lo, int32_t band_hi,
                         double* freq_bin, float* snr, void* stream);
 
+/*
+ * Learned plasma-line estimator (the network maps an integrated spectrum to the line's
+ * position and presence; Eq. 1 links that position to the electron density).  Network:
+ * four 9-tap, 32-channel 1-D convolutions with ReLU over the band's standardised log
+ * power, location logits by a 1x1 convolution, presence by an MLP on the per-channel max
+ * and mean; parameters as a flat float vector of ISR_EST_N_PARAMS in the order
+ * W1[32][1][9] b1[32] W2[32][32][9] b2 W3 b3 W4 b4 w5[32] b5[1] Wa[32][64] ba[32] wb[32] bb[1].
+ * Training keeps FP32 master weights and Adam moments; activations and working weights
+ * use `precision` (ISR_EST_FP32 or ISR_EST_BF16) with FP32 accumulation.  All array
+ * arguments are device memory except where noted; calls are ordered on `stream`.
+ */
+#define ISR_EST_N_PARAMS 30210
+#define ISR_EST_FP32 0
+#define ISR_EST_BF16 1
+typedef struct isr_est isr_est;
+
+/* Estimator for spectra of nfft bins; band [band_lo, band_lo + band_len); batches of up
+ * to max_batch gates.  Parameters start at zero: set them with isr_est_set_params. */
+isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t band_len, int32_t max_batch,
+                          int32_t precision, int32_t device, void* stream);
+/* Copy ISR_EST_N_PARAMS floats in (host or device; resets the Adam state) or out. */
+isr_status isr_est_set_params(isr_est* est, const float* params);
+isr_status isr_est_get_params(isr_est* est, float* params);
+/* x[n][band_len] = (ln P - mean) / (std + 1e-6) over the band, from spectra[n][nfft]. */
+isr_status isr_est_features(isr_est* est, const float* spectra, int32_t n, float* x);
+/* Batch loss and its gradient (no update).  line_bin: true position in bins from band_lo;
+ * present: 1 or 0.  loss (one float) and grad (ISR_EST_N_PARAMS floats) may be host or
+ * device memory or NULL.  Synchronises the stream. */
+isr_status isr_est_grad(isr_est* est, const float* x, int32_t n, const float* line_bin, const float* present,
+                        float* loss, float* grad);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the batch; loss (host or device) optional. */
+isr_status isr_est_train_step(isr_est* est, const float* x, int32_t n, const float* line_bin, const float* present,
+                              float lr, float* loss);
+/* line_bin[n]: position in bins of the full spectrum (band_lo + soft-argmax over the 7 bins
+ * around the largest location logit); presence[n]: sigmoid of the presence logit. */
+isr_status isr_est_predict(isr_est* est, const float* x, int32_t n, float* line_bin, float* presence);
+void isr_est_destroy(isr_est* est);
+
 /* Release the plan and its device memory (synchronises its stream first); NULL is safe. */
 void isr_destroy(isr_plan* plan);
 

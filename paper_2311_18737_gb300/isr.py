@@ -34,7 +34,12 @@ STATUS_NAMES = {0: "ISR_OK", 1: "ISR_ERR_INVALID_ARG", 2: "ISR_ERR_UNSUPPORTED",
 # every entry point declared in include/isr.h
 EXPORTS = ("isr_plan_create", "isr_integrate", "isr_spectra", "isr_plan_query", "isr_plan_set_profiling",
            "isr_plan_set_wait_limit", "isr_plan_test_drop_window", "isr_destroy", "isr_last_error",
-           "isr_integrate_static", "isr_peak_fit")
+           "isr_integrate_static", "isr_peak_fit", "isr_est_create", "isr_est_set_params", "isr_est_get_params",
+           "isr_est_features", "isr_est_grad", "isr_est_train_step", "isr_est_predict", "isr_est_destroy")
+
+ISR_EST_N_PARAMS = 30210
+ISR_EST_FP32 = 0
+ISR_EST_BF16 = 1
 
 # floats of the allocation-free variant's file-scope scratch array
 ISR_STATIC_SCRATCH_FLOATS = 4 * 1024 * 1024
@@ -109,12 +114,22 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isr_plan_test_drop_window.argtypes = [P, ctypes.c_int32]
     lib.isr_integrate_static.argtypes = [ctypes.POINTER(IsrPlanDesc), P, P, ctypes.c_int32, P]
     lib.isr_peak_fit.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P]
+    lib.isr_est_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_int32, ctypes.c_int32, P]
+    lib.isr_est_set_params.argtypes = [P, P]
+    lib.isr_est_get_params.argtypes = [P, P]
+    lib.isr_est_features.argtypes = [P, P, ctypes.c_int32, P]
+    lib.isr_est_grad.argtypes = [P, P, ctypes.c_int32, P, P, P, P]
+    lib.isr_est_train_step.argtypes = [P, P, ctypes.c_int32, P, P, ctypes.c_float, P]
+    lib.isr_est_predict.argtypes = [P, P, ctypes.c_int32, P, P]
+    lib.isr_est_destroy.argtypes = [P]
+    lib.isr_est_destroy.restype = None
     lib.isr_destroy.argtypes = [P]
     lib.isr_destroy.restype = None
     lib.isr_last_error.argtypes = []
     lib.isr_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("isr_destroy", "isr_last_error"):
+        if name not in ("isr_destroy", "isr_last_error", "isr_est_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -199,6 +214,45 @@ def isr_peak_fit(spectra, n_ranges: int, nfft: int, band_lo: int, band_hi: int, 
                  stream=None) -> None:
     _check(load_library().isr_peak_fit(_addr(spectra), int(n_ranges), int(nfft), int(band_lo), int(band_hi),
                                        _addr(freq_bin), _addr(snr), _stream_handle(stream)), "isr_peak_fit")
+
+
+def isr_est_create(nfft: int, band_lo: int, band_len: int, max_batch: int, precision: int = ISR_EST_BF16,
+                   device: int = -1, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().isr_est_create(ctypes.byref(h), int(nfft), int(band_lo), int(band_len), int(max_batch),
+                                         int(precision), int(device), _stream_handle(stream)), "isr_est_create")
+    return h
+
+
+def isr_est_set_params(est, params) -> None:
+    _check(load_library().isr_est_set_params(est, _addr(params)), "isr_est_set_params")
+
+
+def isr_est_get_params(est, params) -> None:
+    _check(load_library().isr_est_get_params(est, _addr(params)), "isr_est_get_params")
+
+
+def isr_est_features(est, spectra, n: int, x) -> None:
+    _check(load_library().isr_est_features(est, _addr(spectra), int(n), _addr(x)), "isr_est_features")
+
+
+def isr_est_grad(est, x, n: int, line_bin, present, loss=None, grad=None) -> None:
+    _check(load_library().isr_est_grad(est, _addr(x), int(n), _addr(line_bin), _addr(present), _addr(loss),
+                                       _addr(grad)), "isr_est_grad")
+
+
+def isr_est_train_step(est, x, n: int, line_bin, present, lr: float, loss=None) -> None:
+    _check(load_library().isr_est_train_step(est, _addr(x), int(n), _addr(line_bin), _addr(present), float(lr),
+                                             _addr(loss)), "isr_est_train_step")
+
+
+def isr_est_predict(est, x, n: int, line_bin, presence) -> None:
+    _check(load_library().isr_est_predict(est, _addr(x), int(n), _addr(line_bin), _addr(presence)),
+           "isr_est_predict")
+
+
+def isr_est_destroy(est) -> None:
+    load_library().isr_est_destroy(est)
 
 
 def isr_destroy(plan) -> None:

@@ -99,9 +99,9 @@ def _host_lib():
             lib.syn_fill_code.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_void_p]
             lib.syn_tone_freqs.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]
-            lib.syn_fill_params.argtypes = [ctypes.POINTER(SynCfg), ctypes.c_void_p, ctypes.c_int,
+            lib.syn_fill_params.argtypes = [ctypes.POINTER(SynCfg), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_void_p]
-            lib.syn_echo_rows.argtypes = [ctypes.POINTER(SynCfg), ctypes.c_void_p, ctypes.c_void_p,
+            lib.syn_echo_rows.argtypes = [ctypes.POINTER(SynCfg), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int]
             lib.syn_echo_rows.restype = ctypes.c_int
             _host = lib
@@ -114,7 +114,7 @@ def _gpu_lib():
         if _gpu is None:
             build_gpu()
             lib = ctypes.CDLL(_GPU_LIB)
-            lib.syn_gpu_echo.argtypes = [ctypes.POINTER(SynCfg), ctypes.c_void_p, ctypes.c_void_p,
+            lib.syn_gpu_echo.argtypes = [ctypes.POINTER(SynCfg), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
             lib.syn_gpu_echo.restype = ctypes.c_int
             _gpu = lib
@@ -145,6 +145,9 @@ class Workload:
     f_hi_hz: float = 15e6
     fwhm_bins: float = 2.0
     snap_to_bins: bool = False
+    # optional per-gate overrides: frequency (cycles/sample) and SNR in dB (-inf: no signal)
+    gate_freq: np.ndarray | None = None
+    gate_snr_db: np.ndarray | None = None
 
     @property
     def amp(self) -> float:
@@ -168,9 +171,19 @@ class Workload:
         c.max_jitter = 64.0 / self.nfft
         return c
 
+    def gate_amps(self) -> np.ndarray | None:
+        """Per-gate signal amplitude (None: ``amp`` for every gate)."""
+        if self.gate_snr_db is None:
+            return None
+        snr = np.asarray(self.gate_snr_db, dtype=np.float64)
+        lin = np.where(np.isfinite(snr), 10.0 ** (np.where(np.isfinite(snr), snr, 0.0) / 10.0), 0.0)
+        return np.ascontiguousarray(np.sqrt(lin * 2.0 * self.sigma ** 2), dtype=np.float64)
+
     def base_freqs(self) -> np.ndarray:
         """Per-gate line/tone frequency in cycles per sample."""
-        if self.kind == LINE:
+        if self.gate_freq is not None:
+            f = np.asarray(self.gate_freq, dtype=np.float64)
+        elif self.kind == LINE:
             r = np.arange(self.n_ranges, dtype=np.float64)
             z = (r - self.chapman_peak_gate) / self.chapman_scale_gates
             ne_rel = np.exp(0.5 * (1.0 - z - np.exp(-z)))  # Chapman layer, n_e / n_max
@@ -199,7 +212,9 @@ class Workload:
         code = np.ascontiguousarray(self.code())
         fb = self.base_freqs()
         out = np.empty((row_end - row_begin, self.echo_stride, 2), dtype=np.int16)
-        rc = _host_lib().syn_echo_rows(ctypes.byref(self.cfg()), fb.ctypes.data, code.ctypes.data,
+        amps = self.gate_amps()
+        rc = _host_lib().syn_echo_rows(ctypes.byref(self.cfg()), fb.ctypes.data,
+                                       None if amps is None else amps.ctypes.data, code.ctypes.data,
                                        row_begin, row_end, out.ctypes.data, n_threads)
         if rc != 0:
             raise MemoryError("synthetic echo generation failed")
@@ -214,7 +229,9 @@ class Workload:
         if row_end is None:
             row_end = self.n_ipp
         fb = self.base_freqs()
-        rc = _gpu_lib().syn_gpu_echo(ctypes.byref(self.cfg()), fb.ctypes.data, code_dev_ptr,
+        amps = self.gate_amps()
+        rc = _gpu_lib().syn_gpu_echo(ctypes.byref(self.cfg()), fb.ctypes.data,
+                                     None if amps is None else amps.ctypes.data, code_dev_ptr,
                                      row_begin, row_end, out_ptr)
         if rc != 0:
             raise RuntimeError(f"device echo generation failed (cudaError {rc})")

@@ -207,8 +207,9 @@ SYN_HD double syn_tone_freq(uint64_t seed, int r)
     return 0.8 * syn_u01(w[0]) - 0.4;
 }
 
-/* amplitude and phase increment of gate r in IPP p; f_base in cycles per sample */
-SYN_HD syn_rp syn_range_params(const syn_cfg* c, double f_base, int r, int p)
+/* amplitude and phase increment of gate r in IPP p; f_base in cycles per sample, amp the
+ * gate's amplitude (tone: |a|; line: rms |a|) */
+SYN_HD syn_rp syn_range_params(const syn_cfg* c, double f_base, double amp, int r, int p)
 {
     uint32_t w[4];
     syn_draw(c->seed, (uint32_t)r, (uint32_t)p, SYN_PURPOSE_LINE, w);
@@ -216,7 +217,7 @@ SYN_HD syn_rp syn_range_params(const syn_cfg* c, double f_base, int r, int p)
     if (c->kind == SYN_LINE) {
         double g0, g1;
         syn_gauss2(w[0], w[1], &g0, &g1);
-        double sc = c->amp * 0.70710678118654752440;
+        double sc = amp * 0.70710678118654752440;
         ar = sc * g0;
         ai = sc * g1;
         /* Cauchy jitter hwhm * tan(pi (u - 1/2)): Lorentzian line of half width hwhm */
@@ -229,8 +230,8 @@ SYN_HD syn_rp syn_range_params(const syn_cfg* c, double f_base, int r, int p)
     } else {
         double s, co;
         syn_sincos_turns(syn_u01(w[0]), &s, &co);
-        ar = c->amp * co;
-        ai = c->amp * s;
+        ar = amp * co;
+        ai = amp * s;
     }
     syn_rp o;
     o.ar = (float)ar;

@@ -34,18 +34,21 @@ void syn_tone_freqs(uint64_t seed, int n, double* out)
     for (int r = 0; r < n; ++r) out[r] = syn_tone_freq(seed, r);
 }
 
-void syn_fill_params(const syn_cfg* c, const double* f_base, int p, syn_rp* out)
+/* amp_gate: per-gate amplitude, or NULL for c->amp everywhere */
+void syn_fill_params(const syn_cfg* c, const double* f_base, const double* amp_gate, int p, syn_rp* out)
 {
-    for (int r = 0; r < c->n_ranges; ++r) out[r] = syn_range_params(c, f_base[r], r, p);
+    for (int r = 0; r < c->n_ranges; ++r)
+        out[r] = syn_range_params(c, f_base[r], amp_gate ? amp_gate[r] : c->amp, r, p);
 }
 
 /*
  * Echo rows [row_begin, row_end) into out[(p - row_begin)][echo_stride][2].
+ * amp_gate: per-gate amplitude or NULL (c->amp for every gate).
  * code: [1][code_len] when per_ipp_code == 0, else rows indexed by absolute p
  *       ([row_end][code_len] at least).
  * Returns 0, or 2 on allocation failure.
  */
-int syn_echo_rows(const syn_cfg* c, const double* f_base, const int8_t* code,
+int syn_echo_rows(const syn_cfg* c, const double* f_base, const double* amp_gate, const int8_t* code,
                   int64_t row_begin, int64_t row_end, int16_t* out, int n_threads)
 {
     float* table = (float*)malloc(sizeof(float) * 2 * SYN_TABLE_SIZE);
@@ -65,7 +68,7 @@ int syn_echo_rows(const syn_cfg* c, const double* f_base, const int8_t* code,
             fail = 1;
             continue;
         }
-        syn_fill_params(c, f_base, (int)p, rp);
+        syn_fill_params(c, f_base, amp_gate, (int)p, rp);
         const int8_t* crow = code + (c->per_ipp_code ? (size_t)p * (size_t)c->code_len : 0);
         int16_t* row = out + (size_t)(p - row_begin) * (size_t)c->echo_stride * 2;
         for (int64_t t = 0; t < c->echo_stride; ++t)

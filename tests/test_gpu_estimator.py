@@ -1,0 +1,83 @@
+"""The learned estimator's kernels (through the C ABI) against the FP64 reference:
+features, loss and every parameter's gradient (FP32 storage), the BF16 variant, the
+prediction, and a short end-to-end training on spectra the integrator produces."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import estimator as ref
+from paper_2311_18737_gb300 import estimator as est_mod
+from paper_2311_18737_gb300 import isr
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(precision, B=4, L=256, seed=0):
+    rng = np.random.default_rng(seed)
+    theta = (ref.init_params(seed) + 0.05 * rng.standard_normal(ref.N_PARAMS)).astype(np.float32)
+    x = rng.standard_normal((B, L)).astype(np.float32)
+    f = rng.uniform(3, L - 3, B).astype(np.float32)
+    y = np.array([1, 0, 1, 1][:B], dtype=np.float32)
+    e = est_mod.Estimator(max_batch=8, precision=precision, nfft=512, band_lo=0, band_len=L)
+    e.set_params(theta)
+    dev = torch.device("cuda:0")
+    return e, theta, x, f, y, [torch.from_numpy(a).to(dev) for a in (x, f, y)]
+
+
+def test_gradients_match_fp64_reference_fp32_storage():
+    e, theta, x, f, y, (xd, fd, yd) = _setup(isr.ISR_EST_FP32)
+    loss, g = e.grad(xd, fd, yd)
+    rl, rg = ref.loss_and_grad(theta.astype(np.float64), x, f, y)
+    assert abs(loss - rl) <= 1e-5 * abs(rl)
+    gd, rd = ref.unpack(g.astype(np.float64)), ref.unpack(rg)
+    for name, _ in ref.SHAPES:
+        scale = np.abs(rd[name]).max() + 1e-12
+        err = np.abs(gd[name] - rd[name]).max() / scale
+        assert err <= 2e-4, f"{name}: max error {err:.2e} of the block's largest gradient"
+    e.close()
+
+
+def test_bf16_storage_close_to_reference():
+    e, theta, x, f, y, (xd, fd, yd) = _setup(isr.ISR_EST_BF16, seed=1)
+    loss, g = e.grad(xd, fd, yd)
+    rl, rg = ref.loss_and_grad(theta.astype(np.float64), x, f, y)
+    assert abs(loss - rl) <= 3e-2 * abs(rl)
+    cos = float(g @ rg / (np.linalg.norm(g) * np.linalg.norm(rg)))
+    assert cos > 0.98, cos
+    e.close()
+
+
+def test_prediction_matches_reference():
+    e, theta, x, f, y, (xd, fd, yd) = _setup(isr.ISR_EST_FP32, seed=2)
+    pos, pres = e.predict(xd)
+    rpos, rpres = ref.predict(theta.astype(np.float64), x)
+    assert np.abs(pos.cpu().numpy() - rpos).max() <= 1e-3
+    assert np.abs(pres.cpu().numpy() - rpres).max() <= 1e-5
+    e.close()
+
+
+def test_features_match_reference():
+    rng = np.random.default_rng(5)
+    P = rng.gamma(30.0, 2.0, size=(6, 512)).astype(np.float32)
+    e = est_mod.Estimator(max_batch=8, precision=isr.ISR_EST_FP32, nfft=512, band_lo=40, band_len=300)
+    x = e.features(torch.from_numpy(P).cuda()).cpu().numpy()
+    assert np.abs(x - ref.features(P, 40, 300)).max() <= 1e-5
+    e.close()
+
+
+@pytest.mark.slow
+def test_training_gains_over_peak_fit():
+    """Short training on integrator-made spectra (reduced from the full 200k-spectrum run):
+    the network must beat the peak fit's presence decision and agree with the peak fit
+    within one bin on strong lines."""
+    e = est_mod.Estimator(max_batch=128, precision=isr.ISR_EST_BF16)
+    e.set_params(est_mod.init_params(0))
+    tr = est_mod.make_dataset(16, seed=11, est=e)
+    te = est_mod.make_dataset(4, seed=12, est=e)
+    hist = est_mod.train(e, tr, steps=600, batch=128, lr=2e-3, log_every=100)
+    assert hist[-1][1] < 0.7 * hist[0][1], hist
+    res = est_mod.evaluate(e, te, est_mod.presence_threshold(tr))
+    print(res)
+    assert res["presence_accuracy"]["network"] >= res["presence_accuracy"]["peak_fit"]
+    assert res["agreement_with_peak_fit_above_-10dB"] >= 0.9
+    e.close()
