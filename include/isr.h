@@ -223,6 +223,56 @@ isr_status isr_est_train_step(isr_est* est, const float* x, int32_t n, const flo
 isr_status isr_est_predict(isr_est* est, const float* x, int32_t n, float* line_bin, float* presence);
 void isr_est_destroy(isr_est* est);
 
+/*
+ * Batched integration of many windows of uneven shape in one persistent launch.  Radars
+ * integrate several windows at once, e.g. the up- and down-shifted plasma-line channels
+ * (the line appears at +-f_r, Sec. 2.1) with different range extents and resolutions.
+ * Each window is an independent integration (Eqs. 7-8) with its own echo, code and
+ * geometry; isr_batch_run writes, for every window, the sum over its n_ipp IPPs as float
+ * [n_ranges][nfft] into its `out`.  All (gate group, IPP chunk) units of all windows
+ * form one queue, longest first, served by one CTA per SM.  Buffers are device memory and
+ * stay bound to the batch: refill them between runs.  Limits: nfft in {2048, 4096, 8192,
+ * 16384}; binary-phase codes (ISR_TX_PM1) only.
+ */
+typedef struct {
+    const int16_t* echo;  /* [n_ipp][echo_stride][2], 16-byte aligned */
+    const void* tx_code;  /* int8 chips, [1 or n_ipp rows][tx_stride] */
+    float* out;           /* [n_ranges][nfft] sums */
+    int64_t echo_stride;  /* multiple of 4 */
+    int64_t tx_stride;    /* 0 = one code for every IPP */
+    int32_t nfft;
+    int32_t code_len;
+    int32_t n_ranges;
+    int32_t range_start;
+    int32_t range_step;
+    int32_t n_ipp;
+    int32_t order;        /* Stockham radix order 0..2, or -1 = default / autotuned */
+    int32_t reserved;
+} isr_window;
+
+#define ISR_BATCH_GRAPH 1    /* capture launch + reduction in a CUDA graph; runs replay it */
+#define ISR_BATCH_AUTOTUNE 2 /* at creation, time the radix orders of each nfft on these windows */
+
+typedef struct {
+    int32_t n_windows;
+    int32_t graph;          /* 1 if runs replay a captured graph */
+    int64_t n_units;        /* work units per run */
+    int64_t transforms;     /* gate-IPP transforms per run */
+    int32_t order[4];       /* radix order used for nfft 2048, 4096, 8192, 16384 */
+    float tune_ms[4][3];    /* probe time of each order (0 if not tuned) */
+} isr_batch_info;
+
+typedef struct isr_batch isr_batch;
+
+isr_status isr_batch_create(isr_batch** out, const isr_window* windows, int32_t n_windows, int32_t flags,
+                            int32_t device, void* stream);
+/* Enqueue one run on the batch's stream (asynchronous). */
+isr_status isr_batch_run(isr_batch* batch);
+/* Wait for the batch's stream; ISR_ERR_TIMEOUT if a unit's bounded wait ran out. */
+isr_status isr_batch_wait(isr_batch* batch);
+isr_status isr_batch_query(const isr_batch* batch, isr_batch_info* info);
+void isr_batch_destroy(isr_batch* batch);
+
 /* Release the plan and its device memory (synchronises its stream first); NULL is safe. */
 void isr_destroy(isr_plan* plan);
 

@@ -82,9 +82,12 @@ def conv(h, W, b):
 
 
 def target(f_true, L):
+    """Gaussian location target per gate; all zeros where the line lies too far outside
+    the band for the target to be representable (such gates carry no line)."""
     i = np.arange(L)[None, :]
     t = np.exp(-((i - np.asarray(f_true, dtype=np.float64)[:, None]) ** 2) / (2 * SIGMA_T ** 2))
-    return t / t.sum(axis=1, keepdims=True)
+    s = t.sum(axis=1, keepdims=True)
+    return np.where(s > 0, t / np.where(s > 0, s, 1.0), 0.0)
 
 
 def forward(theta, x):
@@ -116,7 +119,7 @@ def loss(theta, x, f_true, y):
     logp = logp - np.log(np.exp(logp).sum(axis=1, keepdims=True))
     ce = -(target(f_true, z.shape[1]) * logp).sum(axis=1)
     bce = np.maximum(q, 0) - q * y + np.log1p(np.exp(-np.abs(q)))
-    return float(np.mean(bce + y * ce))
+    return float(np.mean(bce + np.where(y > 0, y * ce, 0.0)))
 
 
 def loss_and_grad(theta, x, f_true, y):
@@ -129,11 +132,11 @@ def loss_and_grad(theta, x, f_true, y):
     logp = np.log(np.maximum(pi, 1e-300))
     ce = -(t * logp).sum(axis=1)
     bce = np.maximum(q, 0) - q * y + np.log1p(np.exp(-np.abs(q)))
-    total = float(np.mean(bce + y * ce))
+    total = float(np.mean(bce + np.where(y > 0, y * ce, 0.0)))
 
     g = {name: np.zeros(shp) for name, shp in SHAPES}
     dq = (1.0 / (1.0 + np.exp(-q)) - y) / B
-    dz = y[:, None] * (pi - t) / B
+    dz = np.where((y > 0)[:, None], y[:, None] * (pi - t), 0.0) / B
     u, pooled, h4 = cache["u"], cache["pooled"], cache["h4"]
     g["wb"] = dq @ u
     g["bb"][0] = dq.sum()

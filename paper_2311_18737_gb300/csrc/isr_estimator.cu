@@ -371,9 +371,9 @@ __global__ void __launch_bounds__(256) head_bwd_kernel(const T* __restrict__ h4,
     if (threadIdx.x < CH) w5[threadIdx.x] = theta[OFF_W5 + threadIdx.x];
     if (threadIdx.x == 0) {
         // CE = lse - sum t z / sum t ; BCE in the stable form
-        const float ce = st > 0.f ? lse - stz / st : 0.f;
+        const float ce = (y > 0.f && st > 0.f) ? y * (lse - stz / st) : 0.f;
         const float bce = fmaxf(qb, 0.f) - qb * y + log1pf(__expf(-fabsf(qb)));
-        atomicAdd(loss, (bce + y * ce) * invB);
+        atomicAdd(loss, (bce + ce) * invB);
         atomicAdd(&grad[OFF_BB], dq);
     }
     // presence MLP backward (threads 0..31)
@@ -399,11 +399,14 @@ __global__ void __launch_bounds__(256) head_bwd_kernel(const T* __restrict__ h4,
 #pragma unroll
     for (int c = 0; c < CH; ++c) dw5[c] = 0.f;
     float db5 = 0.f;
-    const float inv_st = st > 0.f ? 1.f / st : 0.f;
+    // the location term exists only for gates with a line (its target may lie anywhere,
+    // even outside the band, for gates without one)
+    const bool loc = y > 0.f && st > 0.f;
+    const float inv_st = loc ? 1.f / st : 0.f;
     for (int i = threadIdx.x; i < L; i += 256) {
         const float d = (i - f) / SIGMA_T;
-        const float t = __expf(-0.5f * d * d) * inv_st;
-        const float dz = y * (__expf(zb[i] - lse) - t) * invB;
+        const float t = loc ? __expf(-0.5f * d * d) * inv_st : 0.f;
+        const float dz = loc ? y * (__expf(zb[i] - lse) - t) * invB : 0.f;
         db5 += dz;
 #pragma unroll
         for (int c = 0; c < CH; ++c) {

@@ -26,7 +26,24 @@ enum TxKind { TX_CI16 = 0, TX_C32 = 1, TX_PM1 = 2 };
 constexpr int kThreads = 512;
 
 // ---------------------------------------------------------------- per-size schedule
-template <int LOG2N>
+// Radix orders of the three-pass sizes (nfft 2048 .. 16384).  ORDER 0 is the default;
+// the batched launch may pick another per size (autotuned).
+__host__ __device__ constexpr int radix_of(int log2n, int order, int p)
+{
+    if (log2n <= 5) return p == 0 ? (1 << log2n) : 1;
+    if (log2n <= 10) {
+        constexpr int a0[5] = {8, 16, 16, 32, 32}, a1[5] = {8, 8, 16, 16, 32};
+        return p == 0 ? a0[log2n - 6] : p == 1 ? a1[log2n - 6] : 1;
+    }
+    constexpr int t11[3][3] = {{16, 16, 8}, {8, 16, 16}, {32, 8, 8}};
+    constexpr int t12[3][3] = {{16, 16, 16}, {32, 16, 8}, {8, 16, 32}};
+    constexpr int t13[3][3] = {{32, 16, 16}, {16, 16, 32}, {16, 32, 16}};
+    constexpr int t14[3][3] = {{32, 32, 16}, {16, 32, 32}, {32, 16, 32}};
+    return log2n == 11 ? t11[order][p] : log2n == 12 ? t12[order][p] : log2n == 13 ? t13[order][p] : t14[order][p];
+}
+constexpr int kOrders = 3;
+
+template <int LOG2N, int ORDER = 0>
 struct Sched {
     static constexpr int N = 1 << LOG2N;
     static constexpr int E = N < 32 ? N : 32;   // points per thread
@@ -34,13 +51,9 @@ struct Sched {
     static constexpr int G = kThreads / T;      // transforms (gates) per CTA
     // radices of the Stockham passes, first to last
     static constexpr int NP = LOG2N <= 5 ? 1 : LOG2N <= 10 ? 2 : 3;
-    static constexpr int R0 = LOG2N == 3 ? 8 : LOG2N == 4 ? 16 : LOG2N == 5 ? 32
-                            : LOG2N == 6 ? 8 : LOG2N == 7 ? 16 : LOG2N == 8 ? 16
-                            : LOG2N == 9 ? 32 : LOG2N == 10 ? 32 : LOG2N == 11 ? 16
-                            : LOG2N == 12 ? 16 : 32;
-    static constexpr int R1 = LOG2N <= 5 ? 1 : LOG2N == 6 ? 8 : LOG2N == 7 ? 8 : LOG2N == 8 ? 16
-                            : LOG2N == 9 ? 16 : LOG2N == 10 ? 32 : LOG2N == 14 ? 32 : 16;
-    static constexpr int R2 = LOG2N <= 10 ? 1 : LOG2N == 11 ? 8 : 16;
+    static constexpr int R0 = radix_of(LOG2N, ORDER, 0);
+    static constexpr int R1 = radix_of(LOG2N, ORDER, 1);
+    static constexpr int R2 = radix_of(LOG2N, ORDER, 2);
     static_assert(R0 * R1 * R2 == N, "radix product must equal nfft");
     __host__ __device__ static constexpr int radix(int p) { return p == 0 ? R0 : p == 1 ? R1 : R2; }
     // Twiddles of pass p >= 1: w^k with w = exp(-2 pi i (j mod Ns) / (Ns R)).  A pass whose
@@ -61,7 +74,8 @@ struct Sched {
     static constexpr int STAGE_WORDS = N + 4;   // window + alignment slack, 16-byte multiple
     // dynamic shared-memory layout (bytes)
     static constexpr int OFF_MBAR = 0;
-    static constexpr int OFF_TW = 16 * ((8 * G + 15) / 16);
+    // at least 8 mbarrier slots: the batched launch keeps slots 0..7 alive across shapes
+    static constexpr int OFF_TW = 16 * ((8 * (G < 8 ? 8 : G) + 15) / 16);
     static constexpr int OFF_TAB = OFF_TW + 16 * ((8 * NSLOT * T + 15) / 16);
     static constexpr int OFF_STAGE = OFF_TAB + 16 * ((8 * (TAB1 + TAB2) + 15) / 16);
     static constexpr int OFF_XCH = OFF_STAGE + 4 * STAGE_WORDS * G;
@@ -198,10 +212,10 @@ __device__ __forceinline__ float2 decode(uint32_t w, const void* txrow, int pos,
 }
 
 // sign bits of the code chips a thread decodes in the first pass (bit b*R0 + k)
-template <int LOG2N>
+template <int LOG2N, int ORDER>
 __device__ __forceinline__ uint32_t load_signs(const int8_t* row, int t, int code_len)
 {
-    using S = Sched<LOG2N>;
+    using S = Sched<LOG2N, ORDER>;
     uint32_t m = 0;
     static_for<S::E / S::R0>([&](auto Bc) {
         constexpr int b = decltype(Bc)::value;
@@ -237,17 +251,22 @@ __device__ __forceinline__ void twiddle_tab(float2* v, const float2* tab, int jm
     });
 }
 
-// ---------------------------------------------------------------- the fused kernel
-template <int LOG2N, int TXT>
-__global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
+// ---------------------------------------------------------------- the fused work unit
+// One unit = gates [gx G, gx G + G) of IPP chunk c of the launch `a`.  Each gate group g
+// owns mbarrier slot g (initialised by the caller); phase0 is the number of phases that
+// slot has completed before this unit (units run back to back in the batched launch).
+// setup = false reuses the twiddle tables left by the previous unit of the same shape.
+// Returns false if a staged-window wait ran out.
+template <int LOG2N, int TXT, int ORDER = 0>
+__device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, const int c, unsigned char* smem,
+                                               const uint32_t phase0, const bool setup)
 {
-    using S = Sched<LOG2N>;
+    using S = Sched<LOG2N, ORDER>;
     constexpr int N = S::N, E = S::E, T = S::T, G = S::G, NP = S::NP;
     constexpr int R0 = S::R0;
     constexpr int RL = S::radix(NP - 1);  // radix of the last pass
     // transforms of 32 or fewer threads live inside one warp and sync per warp
     constexpr bool CTA_SYNC = T > 32;
-    extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
     float2* twb = reinterpret_cast<float2*>(smem + S::OFF_TW);
     float2* tab = reinterpret_cast<float2*>(smem + S::OFF_TAB);
@@ -255,10 +274,9 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
     const int tid = threadIdx.x;
     const int g = tid / T;
     const int t = tid - g * T;
-    const int r = blockIdx.x * G + g;
+    const int r = gx * G + g;
     const bool valid = r < a.n_ranges;
     const int64_t s_r = (int64_t)a.range_start + (int64_t)(valid ? r : a.n_ranges - 1) * a.range_step;
-    const int c = blockIdx.y;
     const int p_begin = c * a.chunk_len;
     const int p_end = min(p_begin + a.chunk_len, a.n_ipp);
 
@@ -274,9 +292,10 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
         bulk_load(smem_u32(stage), src, copy_bytes, bar);
     };
 
-    if (t == 0) mbar_init(bar, 1);
+    // the previous unit of this CTA may still read the tables and the exchange buffer
+    if (setup) __syncthreads();
     // per-thread twiddle bases of the recurrence passes, slot-major: [slot][t]
-    for (int i = tid; i < S::NSLOT * T; i += kThreads) {
+    for (int i = tid; i < (setup ? S::NSLOT * T : 0); i += kThreads) {
         int slot = i / T, tt = i - slot * T;
         int pass = slot < S::SLOTS1 ? 1 : 2;
         int b = pass == 1 ? slot : slot - S::SLOTS1;
@@ -287,7 +306,7 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
         twb[i] = make_float2((float)cs, (float)sn);
     }
     // twiddle tables of the small passes: [k - 1][jm] = exp(-2 pi i jm k / (Ns R))
-    for (int i = tid; i < S::TAB1 + S::TAB2; i += kThreads) {
+    for (int i = tid; i < (setup ? S::TAB1 + S::TAB2 : 0); i += kThreads) {
         int pass = i < S::TAB1 ? 1 : 2;
         int e = pass == 1 ? i : i - S::TAB1;
         int ns = S::ns(pass), R = S::radix(pass);
@@ -296,7 +315,6 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
         sincospi(-2.0 * (double)(jm * k) / (double)(ns * R), &sn, &cs);
         tab[i] = make_float2((float)cs, (float)sn);
     }
-    fence_barrier_init();
     __syncthreads();
 
     if (t == 0 && p_begin < p_end && p_begin != a.drop_ipp) issue(p_begin);
@@ -305,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
     constexpr int CHIP = TXT == TX_CI16 ? 4 : TXT == TX_C32 ? 8 : 1;
     uint32_t signs = 0;
     if constexpr (TXT == TX_PM1) {
-        if (a.tx_stride == 0) signs = load_signs<LOG2N>(reinterpret_cast<const int8_t*>(txbase), t, a.code_len);
+        if (a.tx_stride == 0) signs = load_signs<LOG2N, ORDER>(reinterpret_cast<const int8_t*>(txbase), t, a.code_len);
     }
 
     float acc[E];
@@ -316,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
     bool timed_out = false;
     int it = 0;
     for (int p = p_begin; p < p_end; ++p, ++it) {
-        const bool ok = mbar_wait(bar, (uint32_t)(it & 1), a.wait_limit);
+        const bool ok = mbar_wait(bar, (phase0 + (uint32_t)it) & 1u, a.wait_limit);
         // every thread of the CTA agrees before anyone leaves; this barrier also orders the
         // previous IPP's last-pass reads of xch before this IPP's first-pass writes
         const bool any_fail = CTA_SYNC ? __syncthreads_or(!ok) : __any_sync(0xffffffffu, !ok);
@@ -326,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
         }
         const char* txrow = txbase + (size_t)p * (size_t)a.tx_stride * CHIP;
         if constexpr (TXT == TX_PM1) {
-            if (a.tx_stride != 0) signs = load_signs<LOG2N>(reinterpret_cast<const int8_t*>(txrow), t, a.code_len);
+            if (a.tx_stride != 0) signs = load_signs<LOG2N, ORDER>(reinterpret_cast<const int8_t*>(txrow), t, a.code_len);
         }
 
         // ---- pass 0: decode from the staged window, radix-R0 DFT
@@ -411,8 +429,8 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
     if (timed_out) {
         if (tid == 0) atomicOr(a.status, 1);
         // let the copy still in flight land before the CTA's shared memory is released
-        mbar_wait(bar, (uint32_t)(it & 1), a.wait_limit);
-        return;
+        mbar_wait(bar, (phase0 + (uint32_t)it) & 1u, a.wait_limit);
+        return false;
     }
 
     // ---- chunk partials: bin of acc[b*RL + q] is j + q * N / RL, j = t + T b
@@ -427,6 +445,19 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
             });
         });
     }
+    return true;
+}
+
+// One-shot launch: grid = (gate groups, IPP chunks), one unit per CTA.
+template <int LOG2N, int TXT>
+__global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
+{
+    using S = Sched<LOG2N>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
+    if (threadIdx.x < S::G) mbar_init(smem_u32(&mbar[threadIdx.x]), 1);
+    fence_barrier_init();
+    integrate_unit<LOG2N, TXT, 0>(a, blockIdx.x, blockIdx.y, smem, 0u, true);
 }
 
 }  // namespace isr

@@ -35,7 +35,11 @@ STATUS_NAMES = {0: "ISR_OK", 1: "ISR_ERR_INVALID_ARG", 2: "ISR_ERR_UNSUPPORTED",
 EXPORTS = ("isr_plan_create", "isr_integrate", "isr_spectra", "isr_plan_query", "isr_plan_set_profiling",
            "isr_plan_set_wait_limit", "isr_plan_test_drop_window", "isr_destroy", "isr_last_error",
            "isr_integrate_static", "isr_peak_fit", "isr_est_create", "isr_est_set_params", "isr_est_get_params",
-           "isr_est_features", "isr_est_grad", "isr_est_train_step", "isr_est_predict", "isr_est_destroy")
+           "isr_est_features", "isr_est_grad", "isr_est_train_step", "isr_est_predict", "isr_est_destroy",
+           "isr_batch_create", "isr_batch_run", "isr_batch_wait", "isr_batch_query", "isr_batch_destroy")
+
+ISR_BATCH_GRAPH = 1
+ISR_BATCH_AUTOTUNE = 2
 
 ISR_EST_N_PARAMS = 30210
 ISR_EST_FP32 = 0
@@ -87,6 +91,40 @@ class IsrPlanInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class IsrWindow(ctypes.Structure):
+    _fields_ = [
+        ("echo", ctypes.c_void_p),
+        ("tx_code", ctypes.c_void_p),
+        ("out", ctypes.c_void_p),
+        ("echo_stride", ctypes.c_int64),
+        ("tx_stride", ctypes.c_int64),
+        ("nfft", ctypes.c_int32),
+        ("code_len", ctypes.c_int32),
+        ("n_ranges", ctypes.c_int32),
+        ("range_start", ctypes.c_int32),
+        ("range_step", ctypes.c_int32),
+        ("n_ipp", ctypes.c_int32),
+        ("order", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class IsrBatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_windows", ctypes.c_int32),
+        ("graph", ctypes.c_int32),
+        ("n_units", ctypes.c_int64),
+        ("transforms", ctypes.c_int64),
+        ("order", ctypes.c_int32 * 4),
+        ("tune_ms", (ctypes.c_float * 3) * 4),
+    ]
+
+    def as_dict(self):
+        return {"n_windows": self.n_windows, "graph": bool(self.graph), "n_units": self.n_units,
+                "transforms": self.transforms, "order": list(self.order),
+                "tune_ms": [list(r) for r in self.tune_ms]}
+
+
 class IsrError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
@@ -124,12 +162,19 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isr_est_predict.argtypes = [P, P, ctypes.c_int32, P, P]
     lib.isr_est_destroy.argtypes = [P]
     lib.isr_est_destroy.restype = None
+    lib.isr_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(IsrWindow), ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32, P]
+    lib.isr_batch_run.argtypes = [P]
+    lib.isr_batch_wait.argtypes = [P]
+    lib.isr_batch_query.argtypes = [P, ctypes.POINTER(IsrBatchInfo)]
+    lib.isr_batch_destroy.argtypes = [P]
+    lib.isr_batch_destroy.restype = None
     lib.isr_destroy.argtypes = [P]
     lib.isr_destroy.restype = None
     lib.isr_last_error.argtypes = []
     lib.isr_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("isr_destroy", "isr_last_error", "isr_est_destroy"):
+        if name not in ("isr_destroy", "isr_last_error", "isr_est_destroy", "isr_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -253,6 +298,32 @@ def isr_est_predict(est, x, n: int, line_bin, presence) -> None:
 
 def isr_est_destroy(est) -> None:
     load_library().isr_est_destroy(est)
+
+
+def isr_batch_create(windows, flags: int = 0, device: int = -1, stream=None) -> ctypes.c_void_p:
+    arr = (IsrWindow * len(windows))(*windows)
+    h = ctypes.c_void_p()
+    _check(load_library().isr_batch_create(ctypes.byref(h), arr, len(windows), int(flags), int(device),
+                                           _stream_handle(stream)), "isr_batch_create")
+    return h
+
+
+def isr_batch_run(batch) -> None:
+    _check(load_library().isr_batch_run(batch), "isr_batch_run")
+
+
+def isr_batch_wait(batch) -> None:
+    _check(load_library().isr_batch_wait(batch), "isr_batch_wait")
+
+
+def isr_batch_query(batch) -> IsrBatchInfo:
+    info = IsrBatchInfo()
+    _check(load_library().isr_batch_query(batch, ctypes.byref(info)), "isr_batch_query")
+    return info
+
+
+def isr_batch_destroy(batch) -> None:
+    load_library().isr_batch_destroy(batch)
 
 
 def isr_destroy(plan) -> None:

@@ -30,6 +30,16 @@ def test_backward_matches_finite_differences():
         assert abs(num - g[i]) <= 1e-6 + 1e-5 * abs(num), (i, num, g[i])
 
 
+def test_gate_without_line_ignores_its_position():
+    theta, x, f, y = _case(6)
+    f2 = f.copy()
+    f2[1] = -500.0                      # y[1] == 0: any position, even far outside the band
+    L1, g1 = est.loss_and_grad(theta, x, f, y)
+    L2, g2 = est.loss_and_grad(theta, x, f2, y)
+    assert np.isfinite(L2) and np.all(np.isfinite(g2))
+    assert abs(L1 - L2) < 1e-12 and np.allclose(g1, g2, atol=1e-15)
+
+
 def test_every_block_has_a_gradient():
     theta, x, f, y = _case(3)
     _, g = est.loss_and_grad(theta, x, f, y)

@@ -18,6 +18,7 @@ def _setup(precision, B=4, L=256, seed=0):
     x = rng.standard_normal((B, L)).astype(np.float32)
     f = rng.uniform(3, L - 3, B).astype(np.float32)
     y = np.array([1, 0, 1, 1][:B], dtype=np.float32)
+    f[1] = -320.0                      # a gate without a line: its position is meaningless
     e = est_mod.Estimator(max_batch=8, precision=precision, nfft=512, band_lo=0, band_len=L)
     e.set_params(theta)
     dev = torch.device("cuda:0")
@@ -30,8 +31,11 @@ def test_gradients_match_fp64_reference_fp32_storage():
     rl, rg = ref.loss_and_grad(theta.astype(np.float64), x, f, y)
     assert abs(loss - rl) <= 1e-5 * abs(rl)
     gd, rd = ref.unpack(g.astype(np.float64)), ref.unpack(rg)
+    gmax = np.abs(rg).max()
     for name, _ in ref.SHAPES:
-        scale = np.abs(rd[name]).max() + 1e-12
+        # b5 shifts every location logit equally, so its exact gradient is 0: measure such
+        # blocks against the overall gradient scale
+        scale = max(np.abs(rd[name]).max(), 1e-3 * gmax)
         err = np.abs(gd[name] - rd[name]).max() / scale
         assert err <= 2e-4, f"{name}: max error {err:.2e} of the block's largest gradient"
     e.close()
