@@ -140,6 +140,12 @@ isr_status isr_plan_set_profiling(isr_plan* plan, int32_t enable);
  * and return; the next isr_spectra reports ISR_ERR_TIMEOUT.  polls must be > 0. */
 isr_status isr_plan_set_wait_limit(isr_plan* plan, uint32_t polls);
 
+/* Stockham radix order (0..2) of the kernel used for binary-phase codes with
+ * code_len == nfft, for nfft >= 2048 (smaller sizes have one order).  Every order gives
+ * the same spectra up to FP32 rounding; they differ in speed, so a caller (or the
+ * binding's autotuner) may time them and keep the fastest.  Default 0. */
+isr_status isr_plan_set_order(isr_plan* plan, int32_t order);
+
 /* Test hook: the kernels of the following isr_integrate calls never stage the window of
  * IPP `ipp` (counted from the first IPP of each call; -1 turns the hook off), so its wait
  * runs out and exercises the timeout path above without any fault. */

@@ -127,6 +127,7 @@ struct isr_plan {
     int64_t launches = 0;
     unsigned wait_limit = kDefaultWaitLimit;
     int drop_ipp = -1;
+    int order = 0;  // radix order of the full-length binary-phase kernel
     // profiling of the fused kernel
     bool prof = false;
     std::vector<cudaEvent_t> ev_free;
@@ -225,8 +226,11 @@ isr_status launch_block(isr_plan* p, const uint32_t* echo, const char* tx, int64
             if (ev.first && ev.second) CUDA_TRY(cudaEventRecord(ev.first, p->stream));
         }
         void* args[] = {&a};
-        CUDA_TRY(cudaLaunchKernel(p->ke.fn, dim3((unsigned)rg, (unsigned)C), dim3((unsigned)p->ke.threads), args,
-                                  (size_t)p->ke.smem, p->stream));
+        const bool full = p->d.code_len == p->d.nfft;
+        const void* fn = full ? p->ke.fn_order[p->order] : p->ke.fn;
+        const int smem = full ? p->ke.smem_order[p->order] : p->ke.smem;
+        CUDA_TRY(cudaLaunchKernel(fn, dim3((unsigned)rg, (unsigned)C), dim3((unsigned)p->ke.threads), args,
+                                  (size_t)smem, p->stream));
         if (p->prof && ev.first && ev.second) {
             CUDA_TRY(cudaEventRecord(ev.second, p->stream));
             p->ev_pending.push_back(ev);
@@ -360,6 +364,8 @@ isr_status isr_plan_create(isr_plan** out, const isr_plan_desc* desc)
     if (p->ke.smem > smem_optin)
         return bail(fail(ISR_ERR_UNSUPPORTED, "kernel needs %d B shared memory, device allows %d", p->ke.smem, smem_optin));
     e = cudaFuncSetAttribute(p->ke.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->ke.smem);
+    for (int o = 0; o < 3 && e == cudaSuccess; ++o)
+        e = cudaFuncSetAttribute(p->ke.fn_order[o], cudaFuncAttributeMaxDynamicSharedMemorySize, p->ke.smem_order[o]);
     if (e != cudaSuccess) return bail(fail(ISR_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
 
     const int64_t RN = (int64_t)d.n_ranges * d.nfft;
@@ -485,6 +491,14 @@ isr_status isr_plan_set_wait_limit(isr_plan* p, uint32_t polls)
 {
     if (!p || polls == 0) return fail(ISR_ERR_INVALID_ARG, "plan is NULL or polls is 0");
     p->wait_limit = polls;
+    return ISR_OK;
+}
+
+isr_status isr_plan_set_order(isr_plan* p, int32_t order)
+{
+    if (!p || order < 0 || order > 2) return fail(ISR_ERR_INVALID_ARG, "plan is NULL or order not in 0..2");
+    if (p->d.nfft < 2048 && order != 0) return fail(ISR_ERR_UNSUPPORTED, "radix orders exist for nfft >= 2048 only");
+    p->order = order;
     return ISR_OK;
 }
 

@@ -256,8 +256,9 @@ __device__ __forceinline__ void twiddle_tab(float2* v, const float2* tab, int jm
 // owns mbarrier slot g (initialised by the caller); phase0 is the number of phases that
 // slot has completed before this unit (units run back to back in the batched launch).
 // setup = false reuses the twiddle tables left by the previous unit of the same shape.
+// FULL = true promises code_len == nfft (no zero padding, no per-sample bound check).
 // Returns false if a staged-window wait ran out.
-template <int LOG2N, int TXT, int ORDER = 0>
+template <int LOG2N, int TXT, int ORDER = 0, bool FULL = false>
 __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, const int c, unsigned char* smem,
                                                const uint32_t phase0, const bool setup)
 {
@@ -357,7 +358,7 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
                 const int pos = j + k * (N / R0);
                 // chips at or past code_len are the zero padding (and are never read)
                 u[k] = make_float2(0.f, 0.f);
-                if (pos < a.code_len)
+                if (FULL || pos < a.code_len)
                     u[k] = decode<TXT>(stage[off + pos], txrow, pos, (signs << (31 - (b * R0 + k))) & 0x80000000u);
             });
             dft<R0>(u);
@@ -449,15 +450,15 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
 }
 
 // One-shot launch: grid = (gate groups, IPP chunks), one unit per CTA.
-template <int LOG2N, int TXT>
+template <int LOG2N, int TXT, bool FULL = false, int ORDER = 0>
 __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
 {
-    using S = Sched<LOG2N>;
+    using S = Sched<LOG2N, ORDER>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
     if (threadIdx.x < S::G) mbar_init(smem_u32(&mbar[threadIdx.x]), 1);
     fence_barrier_init();
-    integrate_unit<LOG2N, TXT, 0>(a, blockIdx.x, blockIdx.y, smem, 0u, true);
+    integrate_unit<LOG2N, TXT, ORDER, FULL>(a, blockIdx.x, blockIdx.y, smem, 0u, true);
 }
 
 }  // namespace isr

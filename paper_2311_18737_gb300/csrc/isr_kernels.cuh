@@ -12,6 +12,9 @@ void clear_error();
 
 struct KernelEntry {
     const void* fn;   // __global__ integrate_kernel<LOG2N, TXT>
+    const void* fn_full;  // the same for code_len == nfft (binary-phase codes only; else fn)
+    const void* fn_order[3];  // fn_full with radix order 0..2 (nfft >= 2048; else fn_full)
+    int smem_order[3];        // their shared memory
     int smem;         // dynamic shared memory bytes
     int gates;        // range gates per CTA (G)
     int threads;      // threads per CTA
@@ -24,7 +27,17 @@ KernelEntry entry_for(int txt)
     const void* f = txt == TX_CI16 ? (const void*)integrate_kernel<L, TX_CI16>
                   : txt == TX_C32  ? (const void*)integrate_kernel<L, TX_C32>
                                    : (const void*)integrate_kernel<L, TX_PM1>;
-    return KernelEntry{f, S::SMEM, S::G, kThreads};
+    const void* ff = txt == TX_PM1 ? (const void*)integrate_kernel<L, TX_PM1, true> : f;
+    KernelEntry e{f, ff, {ff, ff, ff}, {S::SMEM, S::SMEM, S::SMEM}, S::SMEM, S::G, kThreads};
+    if constexpr (L >= 11) {
+        if (txt == TX_PM1) {
+            e.fn_order[1] = (const void*)integrate_kernel<L, TX_PM1, true, 1>;
+            e.fn_order[2] = (const void*)integrate_kernel<L, TX_PM1, true, 2>;
+            e.smem_order[1] = Sched<L, 1>::SMEM;
+            e.smem_order[2] = Sched<L, 2>::SMEM;
+        }
+    }
+    return e;
 }
 
 // defined in the instantiation units (one per group of sizes, compiled in parallel)

@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "ISR_OK", 1: "ISR_ERR_INVALID_ARG", 2: "ISR_ERR_UNSUPPORTED",
 
 # every entry point declared in include/isr.h
 EXPORTS = ("isr_plan_create", "isr_integrate", "isr_spectra", "isr_plan_query", "isr_plan_set_profiling",
-           "isr_plan_set_wait_limit", "isr_plan_test_drop_window", "isr_destroy", "isr_last_error",
+           "isr_plan_set_wait_limit", "isr_plan_set_order", "isr_plan_test_drop_window", "isr_destroy", "isr_last_error",
            "isr_integrate_static", "isr_peak_fit", "isr_est_create", "isr_est_set_params", "isr_est_get_params",
            "isr_est_features", "isr_est_grad", "isr_est_train_step", "isr_est_predict", "isr_est_destroy",
            "isr_batch_create", "isr_batch_run", "isr_batch_wait", "isr_batch_query", "isr_batch_destroy")
@@ -150,6 +150,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isr_plan_set_profiling.argtypes = [P, ctypes.c_int32]
     lib.isr_plan_set_wait_limit.argtypes = [P, ctypes.c_uint32]
     lib.isr_plan_test_drop_window.argtypes = [P, ctypes.c_int32]
+    lib.isr_plan_set_order.argtypes = [P, ctypes.c_int32]
     lib.isr_integrate_static.argtypes = [ctypes.POINTER(IsrPlanDesc), P, P, ctypes.c_int32, P]
     lib.isr_peak_fit.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P]
     lib.isr_est_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -238,6 +239,10 @@ def isr_plan_set_profiling(plan, enable: bool) -> None:
 
 def isr_plan_set_wait_limit(plan, polls: int) -> None:
     _check(load_library().isr_plan_set_wait_limit(plan, int(polls)), "isr_plan_set_wait_limit")
+
+
+def isr_plan_set_order(plan, order: int) -> None:
+    _check(load_library().isr_plan_set_order(plan, int(order)), "isr_plan_set_order")
 
 
 def isr_plan_test_drop_window(plan, ipp: int) -> None:
@@ -375,6 +380,36 @@ class Plan:
 
     def info(self) -> dict:
         return isr_plan_query(self.handle).as_dict()
+
+    def autotune(self, echo, tx_code, n_ipp: int, reps: int = 2) -> dict:
+        """Time the radix orders on ``n_ipp`` IPPs of the caller's data (device buffers) and
+        keep the fastest; the accumulators are left as they were.  Returns the times."""
+        import torch
+        if self.desc.nfft < 2048:
+            return {"order": 0, "ms": [0.0]}
+        stream = torch.cuda.ExternalStream(self.desc.stream) if self.desc.stream else torch.cuda.current_stream()
+        scratch = Plan(nfft=self.desc.nfft, n_ranges=self.desc.n_ranges, echo_stride=self.desc.echo_stride,
+                       code_len=self.desc.code_len, range_start=self.desc.range_start, range_step=self.desc.range_step,
+                       tx_type=self.desc.tx_type, tx_stride=self.desc.tx_stride, ipp_chunk=self.desc.ipp_chunk,
+                       max_chunks=self.desc.max_chunks, device=self.desc.device, stream=self.desc.stream)
+        times = []
+        try:
+            for order in range(3):
+                isr_plan_set_order(scratch.handle, order)
+                scratch.integrate(echo, tx_code, n_ipp)   # warm-up
+                isr_spectra(scratch.handle, None, ISR_RESET_AFTER)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    scratch.integrate(echo, tx_code, n_ipp)
+                e1.record(stream)
+                isr_spectra(scratch.handle, None, ISR_RESET_AFTER)
+                times.append(e0.elapsed_time(e1) / reps)
+        finally:
+            scratch.close()
+        best = int(min(range(3), key=lambda o: times[o]))
+        isr_plan_set_order(self.handle, best)
+        return {"order": best, "ms": times}
 
     def set_profiling(self, enable: bool = True) -> None:
         isr_plan_set_profiling(self.handle, enable)

@@ -61,6 +61,40 @@ def test_code_formats(kind, per, log2n):
     assert_parity(got, ref, what=f"{kind} per={per} nfft={nfft}")
 
 
+@pytest.mark.parametrize("order", [0, 1, 2])
+@pytest.mark.parametrize("log2n", [11, 12, 13, 14])
+def test_radix_orders(log2n, order):
+    rng = np.random.default_rng(31 * log2n + order)
+    nfft = 1 << log2n
+    R, P = 16384 // nfft + 2, 3
+    echo, tx = _rand_case(rng, nfft, R, P, start=2, step=11, L=nfft, kind="pm1", per=False)
+    dev = torch.device("cuda:0")
+    with isr.Plan(nfft=nfft, n_ranges=R, echo_stride=echo.shape[1], range_start=2, range_step=11, device=0,
+                  stream=torch.cuda.current_stream()) as plan:
+        isr.isr_plan_set_order(plan.handle, order)
+        plan.integrate(torch.from_numpy(echo).to(dev), torch.from_numpy(tx).to(dev), P)
+        out, _ = plan.spectra()
+    ref = oracle.integrate(echo, tx, nfft=nfft, n_ranges=R, range_start=2, range_step=11)
+    assert_parity(out.numpy().astype(np.float64), ref, what=f"nfft={nfft} order={order}")
+
+
+def test_autotune_keeps_parity():
+    rng = np.random.default_rng(8)
+    nfft, R, P = 16384, 3, 4
+    echo, tx = _rand_case(rng, nfft, R, P, start=0, step=25, L=nfft, kind="pm1", per=False)
+    dev = torch.device("cuda:0")
+    e, t = torch.from_numpy(echo).to(dev), torch.from_numpy(tx).to(dev)
+    with isr.Plan(nfft=nfft, n_ranges=R, echo_stride=echo.shape[1], range_step=25, device=0,
+                  stream=torch.cuda.current_stream()) as plan:
+        res = plan.autotune(e, t, P)
+        assert res["order"] in (0, 1, 2) and len(res["ms"]) == 3
+        plan.integrate(e, t, P)
+        out, n = plan.spectra()
+    assert n == P
+    ref = oracle.integrate(echo, tx, nfft=nfft, n_ranges=R, range_step=25)
+    assert_parity(out.numpy().astype(np.float64), ref, what="after autotune")
+
+
 def test_small_workload_full():
     """64 gates x nfft 1024 x 100 IPPs: every bin of the whole workload."""
     w = synth.small()
