@@ -146,6 +146,19 @@ isr_status isr_plan_set_wait_limit(isr_plan* plan, uint32_t polls);
  * binding's autotuner) may time them and keep the fastest.  Default 0. */
 isr_status isr_plan_set_order(isr_plan* plan, int32_t order);
 
+/* Engine of the first FFT pass.  ISR_PREC_FP32 (default): SIMT FP32 everywhere.  The
+ * ISR_PREC_TC_* modes (nfft 16384, ISR_TX_PM1, code_len == nfft) compute the first pass
+ * (radix 16 over the window, then radix 32, 32 on the SIMT pipe) as a DFT-matrix GEMM on
+ * the tensor cores with FP32 accumulation: *_SPLIT modes use hi + lo operand splits
+ * (A_hi B_hi + A_hi B_lo + A_lo B_hi) in BF16 or FP16, the others a single BF16 or FP16
+ * product.  Accumulation over IPPs stays FP32 per chunk and FP64 across chunks. */
+#define ISR_PREC_FP32 0
+#define ISR_PREC_TC_BF16_SPLIT 1
+#define ISR_PREC_TC_FP16_SPLIT 2
+#define ISR_PREC_TC_BF16 3
+#define ISR_PREC_TC_FP16 4
+isr_status isr_plan_set_precision(isr_plan* plan, int32_t precision);
+
 /* Test hook: the kernels of the following isr_integrate calls never stage the window of
  * IPP `ipp` (counted from the first IPP of each call; -1 turns the hook off), so its wait
  * runs out and exercises the timeout path above without any fault. */

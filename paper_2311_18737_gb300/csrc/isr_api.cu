@@ -128,6 +128,7 @@ struct isr_plan {
     unsigned wait_limit = kDefaultWaitLimit;
     int drop_ipp = -1;
     int order = 0;  // radix order of the full-length binary-phase kernel
+    int precision = 0;  // ISR_PREC_*: engine of the first FFT pass
     // profiling of the fused kernel
     bool prof = false;
     std::vector<cudaEvent_t> ev_free;
@@ -228,7 +229,11 @@ isr_status launch_block(isr_plan* p, const uint32_t* echo, const char* tx, int64
         void* args[] = {&a};
         const bool full = p->d.code_len == p->d.nfft;
         const void* fn = full ? p->ke.fn_order[p->order] : p->ke.fn;
-        const int smem = full ? p->ke.smem_order[p->order] : p->ke.smem;
+        int smem = full ? p->ke.smem_order[p->order] : p->ke.smem;
+        if (p->precision != ISR_PREC_FP32) {
+            fn = p->ke.fn_tc[p->precision];
+            smem = p->ke.smem_tc;
+        }
         CUDA_TRY(cudaLaunchKernel(fn, dim3((unsigned)rg, (unsigned)C), dim3((unsigned)p->ke.threads), args,
                                   (size_t)smem, p->stream));
         if (p->prof && ev.first && ev.second) {
@@ -499,6 +504,22 @@ isr_status isr_plan_set_order(isr_plan* p, int32_t order)
     if (!p || order < 0 || order > 2) return fail(ISR_ERR_INVALID_ARG, "plan is NULL or order not in 0..2");
     if (p->d.nfft < 2048 && order != 0) return fail(ISR_ERR_UNSUPPORTED, "radix orders exist for nfft >= 2048 only");
     p->order = order;
+    return ISR_OK;
+}
+
+isr_status isr_plan_set_precision(isr_plan* p, int32_t precision)
+{
+    if (!p || precision < ISR_PREC_FP32 || precision > ISR_PREC_TC_FP16)
+        return fail(ISR_ERR_INVALID_ARG, "plan is NULL or unknown precision %d", precision);
+    if (precision != ISR_PREC_FP32) {
+        if (p->d.nfft != 16384 || p->d.tx_type != ISR_TX_PM1 || p->d.code_len != p->d.nfft || !p->ke.fn_tc[precision])
+            return fail(ISR_ERR_UNSUPPORTED, "tensor-core first pass: nfft 16384, ISR_TX_PM1, code_len == nfft only");
+        DeviceGuard guard(p->dev);
+        cudaError_t e = cudaFuncSetAttribute(p->ke.fn_tc[precision], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             p->ke.smem_tc);
+        if (e != cudaSuccess) return fail(ISR_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    }
+    p->precision = precision;
     return ISR_OK;
 }
 

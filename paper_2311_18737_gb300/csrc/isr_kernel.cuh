@@ -18,6 +18,7 @@
 #include <cstdint>
 
 #include "isr_fft.cuh"
+#include "isr_tc.cuh"
 
 namespace isr {
 
@@ -71,7 +72,9 @@ struct Sched {
     // of the passes free of bank conflicts (stride R0 + 1 for the first pass' writes)
     static constexpr int PADP = R0 < 16 ? 16 : R0;
     static constexpr int NPAD = NP > 1 ? N + N / PADP : 0;
-    static constexpr int STAGE_WORDS = N + 4;   // window + alignment slack, 16-byte multiple
+    // window + alignment slack (16-byte multiple); at nfft 16384 room for the padded
+    // 16-row layout of the tensor-core first pass
+    static constexpr int STAGE_WORDS = LOG2N == 14 ? 16 * kTcSeg : N + 4;
     // dynamic shared-memory layout (bytes)
     static constexpr int OFF_MBAR = 0;
     // at least 8 mbarrier slots: the batched launch keeps slots 0..7 alive across shapes
@@ -258,7 +261,9 @@ __device__ __forceinline__ void twiddle_tab(float2* v, const float2* tab, int jm
 // setup = false reuses the twiddle tables left by the previous unit of the same shape.
 // FULL = true promises code_len == nfft (no zero padding, no per-sample bound check).
 // Returns false if a staged-window wait ran out.
-template <int LOG2N, int TXT, int ORDER = 0, bool FULL = false>
+// P0 selects the engine of the first pass: the SIMT radix-R0 DFT, or (nfft 16384, radix
+// order 1, binary-phase, full-length codes only) a split-precision tensor-core GEMM.
+template <int LOG2N, int TXT, int ORDER = 0, bool FULL = false, int P0 = P0_SIMT>
 __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, const int c, unsigned char* smem,
                                                const uint32_t phase0, const bool setup)
 {
@@ -268,6 +273,9 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
     constexpr int RL = S::radix(NP - 1);  // radix of the last pass
     // transforms of 32 or fewer threads live inside one warp and sync per warp
     constexpr bool CTA_SYNC = T > 32;
+    static_assert(P0 == P0_SIMT || (LOG2N == 14 && ORDER == 1 && TXT == TX_PM1 && FULL),
+                  "the tensor-core first pass exists for nfft 16384, radix order 1, full binary-phase codes");
+    uint4* afrag = reinterpret_cast<uint4*>(smem + S::SMEM);   // tensor-core A fragments
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
     float2* twb = reinterpret_cast<float2*>(smem + S::OFF_TW);
     float2* tab = reinterpret_cast<float2*>(smem + S::OFF_TAB);
@@ -290,7 +298,21 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
     const uint32_t copy_bytes = (uint32_t)(((off + a.code_len + 3) & ~3) * 4);
     auto issue = [&](int p) {
         const uint32_t* src = a.echo + (int64_t)p * a.echo_stride + (s_r - off);
-        bulk_load(smem_u32(stage), src, copy_bytes, bar);
+        if constexpr (P0 == P0_SIMT) {
+            bulk_load(smem_u32(stage), src, copy_bytes, bar);
+        } else {
+            // 16 rows of 1024 samples (+4 words of alignment slack, inside the window's row),
+            // each at a 1028-word pitch so the GEMM's column loads hit distinct banks
+            const uint32_t last = off > 0 ? 4u * kTcSeg : 4u * 1024u;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                         "r"(15u * 4u * kTcSeg + last) : "memory");
+            for (int k = 0; k < 16; ++k)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(stage + k * kTcSeg)),
+                    "l"(src + 1024 * k), "r"(k < 15 ? 4u * kTcSeg : last), "r"(bar)
+                    : "memory");
+        }
     };
 
     // the previous unit of this CTA may still read the tables and the exchange buffer
@@ -305,6 +327,9 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
         double sn, cs;
         sincospi(-2.0 * (double)(j % ns) / (double)(ns * R), &sn, &cs);
         twb[i] = make_float2((float)cs, (float)sn);
+    }
+    if constexpr (P0 != P0_SIMT) {
+        if (setup) tc_setup_afrags<P0>(afrag);
     }
     // twiddle tables of the small passes: [k - 1][jm] = exp(-2 pi i jm k / (Ns R))
     for (int i = tid; i < (setup ? S::TAB1 + S::TAB2 : 0); i += kThreads) {
@@ -323,7 +348,9 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
     const char* txbase = reinterpret_cast<const char*>(a.tx);
     constexpr int CHIP = TXT == TX_CI16 ? 4 : TXT == TX_C32 ? 8 : 1;
     uint32_t signs = 0;
-    if constexpr (TXT == TX_PM1) {
+    if constexpr (P0 != P0_SIMT) {
+        if (a.tx_stride == 0) signs = tc_load_signs(reinterpret_cast<const int8_t*>(txbase));
+    } else if constexpr (TXT == TX_PM1) {
         if (a.tx_stride == 0) signs = load_signs<LOG2N, ORDER>(reinterpret_cast<const int8_t*>(txbase), t, a.code_len);
     }
 
@@ -344,12 +371,15 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
             break;
         }
         const char* txrow = txbase + (size_t)p * (size_t)a.tx_stride * CHIP;
-        if constexpr (TXT == TX_PM1) {
+        if constexpr (P0 != P0_SIMT) {
+            if (a.tx_stride != 0) signs = tc_load_signs(reinterpret_cast<const int8_t*>(txrow));
+        } else if constexpr (TXT == TX_PM1) {
             if (a.tx_stride != 0) signs = load_signs<LOG2N, ORDER>(reinterpret_cast<const int8_t*>(txrow), t, a.code_len);
         }
 
         // ---- pass 0: decode from the staged window, radix-R0 DFT
-        static_for<E / R0>([&](auto Bc) {
+        if constexpr (P0 != P0_SIMT) tc_pass0<P0, S::PADP>(stage, off, signs, afrag, xch);
+        else static_for<E / R0>([&](auto Bc) {
             constexpr int b = decltype(Bc)::value;
             const int j = t + T * b;
             float2* u = v + b * R0;
@@ -450,7 +480,7 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
 }
 
 // One-shot launch: grid = (gate groups, IPP chunks), one unit per CTA.
-template <int LOG2N, int TXT, bool FULL = false, int ORDER = 0>
+template <int LOG2N, int TXT, bool FULL = false, int ORDER = 0, int P0 = P0_SIMT>
 __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
 {
     using S = Sched<LOG2N, ORDER>;
@@ -458,7 +488,7 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel(KArgs a)
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
     if (threadIdx.x < S::G) mbar_init(smem_u32(&mbar[threadIdx.x]), 1);
     fence_barrier_init();
-    integrate_unit<LOG2N, TXT, ORDER, FULL>(a, blockIdx.x, blockIdx.y, smem, 0u, true);
+    integrate_unit<LOG2N, TXT, ORDER, FULL, P0>(a, blockIdx.x, blockIdx.y, smem, 0u, true);
 }
 
 }  // namespace isr

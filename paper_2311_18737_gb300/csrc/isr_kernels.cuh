@@ -15,6 +15,8 @@ struct KernelEntry {
     const void* fn_full;  // the same for code_len == nfft (binary-phase codes only; else fn)
     const void* fn_order[3];  // fn_full with radix order 0..2 (nfft >= 2048; else fn_full)
     int smem_order[3];        // their shared memory
+    const void* fn_tc[5];     // [mode] tensor-core first pass (nfft 16384, binary phase); [0] unused
+    int smem_tc;
     int smem;         // dynamic shared memory bytes
     int gates;        // range gates per CTA (G)
     int threads;      // threads per CTA
@@ -28,13 +30,23 @@ KernelEntry entry_for(int txt)
                   : txt == TX_C32  ? (const void*)integrate_kernel<L, TX_C32>
                                    : (const void*)integrate_kernel<L, TX_PM1>;
     const void* ff = txt == TX_PM1 ? (const void*)integrate_kernel<L, TX_PM1, true> : f;
-    KernelEntry e{f, ff, {ff, ff, ff}, {S::SMEM, S::SMEM, S::SMEM}, S::SMEM, S::G, kThreads};
+    KernelEntry e{f, ff, {ff, ff, ff}, {S::SMEM, S::SMEM, S::SMEM}, {nullptr, nullptr, nullptr, nullptr, nullptr},
+                  0, S::SMEM, S::G, kThreads};
     if constexpr (L >= 11) {
         if (txt == TX_PM1) {
             e.fn_order[1] = (const void*)integrate_kernel<L, TX_PM1, true, 1>;
             e.fn_order[2] = (const void*)integrate_kernel<L, TX_PM1, true, 2>;
             e.smem_order[1] = Sched<L, 1>::SMEM;
             e.smem_order[2] = Sched<L, 2>::SMEM;
+        }
+    }
+    if constexpr (L == 14) {
+        if (txt == TX_PM1) {
+            e.fn_tc[1] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_BF16_SPLIT>;
+            e.fn_tc[2] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_FP16_SPLIT>;
+            e.fn_tc[3] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_BF16>;
+            e.fn_tc[4] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_FP16>;
+            e.smem_tc = Sched<14, 1>::SMEM + kTcAfragBytes;
         }
     }
     return e;

@@ -33,10 +33,17 @@ STATUS_NAMES = {0: "ISR_OK", 1: "ISR_ERR_INVALID_ARG", 2: "ISR_ERR_UNSUPPORTED",
 
 # every entry point declared in include/isr.h
 EXPORTS = ("isr_plan_create", "isr_integrate", "isr_spectra", "isr_plan_query", "isr_plan_set_profiling",
-           "isr_plan_set_wait_limit", "isr_plan_set_order", "isr_plan_test_drop_window", "isr_destroy", "isr_last_error",
+           "isr_plan_set_wait_limit", "isr_plan_set_order", "isr_plan_set_precision", "isr_plan_test_drop_window", "isr_destroy", "isr_last_error",
            "isr_integrate_static", "isr_peak_fit", "isr_est_create", "isr_est_set_params", "isr_est_get_params",
            "isr_est_features", "isr_est_grad", "isr_est_train_step", "isr_est_predict", "isr_est_destroy",
            "isr_batch_create", "isr_batch_run", "isr_batch_wait", "isr_batch_query", "isr_batch_destroy")
+
+ISR_PREC_FP32 = 0
+ISR_PREC_TC_BF16_SPLIT = 1
+ISR_PREC_TC_FP16_SPLIT = 2
+ISR_PREC_TC_BF16 = 3
+ISR_PREC_TC_FP16 = 4
+PRECISION_NAMES = {0: "fp32-simt", 1: "tc-bf16-split", 2: "tc-fp16-split", 3: "tc-bf16", 4: "tc-fp16"}
 
 ISR_BATCH_GRAPH = 1
 ISR_BATCH_AUTOTUNE = 2
@@ -151,6 +158,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.isr_plan_set_wait_limit.argtypes = [P, ctypes.c_uint32]
     lib.isr_plan_test_drop_window.argtypes = [P, ctypes.c_int32]
     lib.isr_plan_set_order.argtypes = [P, ctypes.c_int32]
+    lib.isr_plan_set_precision.argtypes = [P, ctypes.c_int32]
     lib.isr_integrate_static.argtypes = [ctypes.POINTER(IsrPlanDesc), P, P, ctypes.c_int32, P]
     lib.isr_peak_fit.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P]
     lib.isr_est_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -243,6 +251,10 @@ def isr_plan_set_wait_limit(plan, polls: int) -> None:
 
 def isr_plan_set_order(plan, order: int) -> None:
     _check(load_library().isr_plan_set_order(plan, int(order)), "isr_plan_set_order")
+
+
+def isr_plan_set_precision(plan, precision: int) -> None:
+    _check(load_library().isr_plan_set_precision(plan, int(precision)), "isr_plan_set_precision")
 
 
 def isr_plan_test_drop_window(plan, ipp: int) -> None:

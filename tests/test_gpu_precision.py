@@ -1,0 +1,64 @@
+"""Tensor-core first pass (split BF16 / FP16 products) against the FP64 oracle; the
+single-product modes must be measurably worse, which is what the split buys."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_helpers import RTOL, assert_parity, rel_err
+from paper_2311_18737_gb300 import isr
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(mode, echo, tx, R, start, step):
+    dev = torch.device("cuda:0")
+    with isr.Plan(nfft=16384, n_ranges=R, echo_stride=echo.shape[1], range_start=start, range_step=step,
+                  device=0, stream=torch.cuda.current_stream()) as plan:
+        if mode:
+            isr.isr_plan_set_precision(plan.handle, mode)
+        plan.integrate(torch.from_numpy(echo).to(dev), torch.from_numpy(tx).to(dev), echo.shape[0])
+        out, _ = plan.spectra()
+    return out.numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def case():
+    rng = np.random.default_rng(41)
+    R, P, start, step = 4, 5, 3, 17       # start 3: windows off the 16-byte grid
+    stride = (start + (R - 1) * step + 16384 + 8 + 3) // 4 * 4
+    echo = np.clip(np.rint(rng.standard_normal((P, stride, 2)) * 3000), -32768, 32767).astype(np.int16)
+    tx = np.where(rng.random(16384) < 0.5, -1, 1).astype(np.int8)
+    ref = oracle.integrate(echo, tx, nfft=16384, n_ranges=R, range_start=start, range_step=step)
+    return echo, tx, R, start, step, ref
+
+
+# Per-bin bounds from the operand precision: FP16 hi + lo carries 22 bits of the DFT matrix
+# (relative 2^-22), so the FP32 tolerance holds; BF16 hi + lo carries 16 bits and the dropped
+# A_lo B_lo term is 2^-16 of a product, so a single IPP's power can be off by ~2 x 2^-16
+# (3e-5); averaging over IPPs shrinks it.
+BOUNDS = {isr.ISR_PREC_TC_FP16_SPLIT: RTOL, isr.ISR_PREC_TC_BF16_SPLIT: 5e-5}
+
+
+@pytest.mark.parametrize("mode", [isr.ISR_PREC_TC_BF16_SPLIT, isr.ISR_PREC_TC_FP16_SPLIT])
+def test_split_modes_within_their_bounds(case, mode):
+    echo, tx, R, start, step, ref = case
+    mx, p99, med = assert_parity(_run(mode, echo, tx, R, start, step), ref, rtol=BOUNDS[mode],
+                                 what=isr.PRECISION_NAMES[mode])
+    print(f"{isr.PRECISION_NAMES[mode]}: max {mx:.2e} p99 {p99:.2e} median {med:.2e}")
+
+
+def test_single_products_are_worse(case):
+    echo, tx, R, start, step, ref = case
+    err = {m: rel_err(_run(m, echo, tx, R, start, step), ref).max()
+           for m in (isr.ISR_PREC_TC_BF16_SPLIT, isr.ISR_PREC_TC_BF16, isr.ISR_PREC_TC_FP16)}
+    assert err[isr.ISR_PREC_TC_BF16] > 10 * err[isr.ISR_PREC_TC_BF16_SPLIT]
+    assert err[isr.ISR_PREC_TC_BF16] > err[isr.ISR_PREC_TC_FP16]
+    assert err[isr.ISR_PREC_TC_BF16] < 0.5
+
+
+def test_unsupported_shapes_rejected():
+    with isr.Plan(nfft=8192, n_ranges=2, echo_stride=9000, device=0, stream=torch.cuda.current_stream()) as plan:
+        with pytest.raises(isr.IsrError) as ei:
+            isr.isr_plan_set_precision(plan.handle, isr.ISR_PREC_TC_BF16_SPLIT)
+        assert ei.value.status == isr.ISR_ERR_UNSUPPORTED
