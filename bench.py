@@ -223,7 +223,13 @@ def run_ours(args):
     plan = isr.Plan(nfft=N, n_ranges=R, echo_stride=w.echo_stride, range_start=w.range_start,
                     range_step=w.range_step, tx_type=isr.ISR_TX_PM1, device=local, stream=stream)
     # radix order: time the candidates on a probe of the workload and keep the fastest
-    tune = plan.autotune(echo, code_d, min(P, 512)) if not args.no_autotune else {"order": 0, "ms": []}
+    if args.order is not None:
+        isr.isr_plan_set_order(plan.handle, args.order)
+        tune = {"order": args.order, "ms": []}
+    elif args.no_autotune:
+        tune = {"order": 0, "ms": []}
+    else:
+        tune = plan.autotune(echo, code_d, min(P, 512))
     plan.set_profiling(True)
 
     def step(e, c, o):
@@ -355,6 +361,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--order", type=int, default=None, help="force a radix order (no autotuning)")
     ap.add_argument("--ref-gates", type=int, default=256)
     ap.add_argument("--ref-ipps", type=int, default=256)
     ap.add_argument("--n-ranges", type=int, default=None, help="resize the workload (profiling cases)")

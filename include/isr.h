@@ -140,8 +140,11 @@ isr_status isr_plan_set_profiling(isr_plan* plan, int32_t enable);
  * and return; the next isr_spectra reports ISR_ERR_TIMEOUT.  polls must be > 0. */
 isr_status isr_plan_set_wait_limit(isr_plan* plan, uint32_t polls);
 
-/* Stockham radix order (0..2) of the kernel used for binary-phase codes with
- * code_len == nfft, for nfft >= 2048 (smaller sizes have one order).  Every order gives
+/* Radix order (0..4) of the kernel used for binary-phase codes with code_len == nfft, for
+ * nfft >= 2048 (smaller sizes have one order): 0..2 are three-pass Stockham orders, 3 is a
+ * radix-(nfft/1024) decimation-in-frequency pass followed by one 1024-point transform per
+ * warp, 4 (nfft 16384 only) the passes [4, 16, 16, 16] with each thread transforming two
+ * butterflies per paired FP32 instruction.  Every order gives
  * the same spectra up to FP32 rounding; they differ in speed, so a caller (or the
  * binding's autotuner) may time them and keep the fastest.  Default 0. */
 isr_status isr_plan_set_order(isr_plan* plan, int32_t order);
@@ -265,7 +268,7 @@ typedef struct {
     int32_t range_start;
     int32_t range_step;
     int32_t n_ipp;
-    int32_t order;        /* Stockham radix order 0..2, or -1 = default / autotuned */
+    int32_t order;        /* radix order 0..3 (see isr_plan_set_order), or -1 = default / autotuned */
     int32_t reserved;
 } isr_window;
 
@@ -278,7 +281,7 @@ typedef struct {
     int64_t n_units;        /* work units per run */
     int64_t transforms;     /* gate-IPP transforms per run */
     int32_t order[4];       /* radix order used for nfft 2048, 4096, 8192, 16384 */
-    float tune_ms[4][3];    /* probe time of each order (0 if not tuned) */
+    float tune_ms[4][4];    /* probe time of each order (0 if not tuned) */
 } isr_batch_info;
 
 typedef struct isr_batch isr_batch;

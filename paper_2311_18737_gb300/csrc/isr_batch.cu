@@ -46,7 +46,8 @@ constexpr int max_smem()
     int m = 0;
     int v[] = {smem_of<11, 0>(), smem_of<11, 1>(), smem_of<11, 2>(), smem_of<12, 0>(), smem_of<12, 1>(),
                smem_of<12, 2>(), smem_of<13, 0>(), smem_of<13, 1>(), smem_of<13, 2>(), smem_of<14, 0>(),
-               smem_of<14, 1>(), smem_of<14, 2>()};
+               smem_of<14, 1>(), smem_of<14, 2>(), isr::SchedWL<11>::SMEM, isr::SchedWL<12>::SMEM,
+               isr::SchedWL<13>::SMEM, isr::SchedWL<14>::SMEM};
     for (int x : v) m = x > m ? x : m;
     return m;
 }
@@ -57,8 +58,14 @@ template <int L, int O>
 __device__ __noinline__ bool run_unit(const BatchWin& w, const BatchUnit& u, unsigned char* smem,
                                       const uint32_t* s_phase, bool setup)
 {
-    using S = isr::Sched<L, O>;
-    return isr::integrate_unit<L, isr::TX_PM1, O>(w.a, u.gx, u.cy, smem, s_phase[threadIdx.x / S::T], setup);
+    if constexpr (O == 3) {
+        using S = isr::SchedWL<L>;
+        return isr::integrate_unit_wl<L, isr::TX_PM1, false>(w.a, u.gx, u.cy, smem, s_phase[threadIdx.x / S::T],
+                                                             setup);
+    } else {
+        using S = isr::Sched<L, O>;
+        return isr::integrate_unit<L, isr::TX_PM1, O>(w.a, u.gx, u.cy, smem, s_phase[threadIdx.x / S::T], setup);
+    }
 }
 
 // Persistent: one CTA per SM pulls work units until the queue is empty.
@@ -91,15 +98,19 @@ __global__ void __launch_bounds__(isr::kThreads, 1) batch_kernel(const BatchWin*
         case 11 * 4 + 0: ok = run_unit<11, 0>(w, u, smem, s_phase, setup); break;
         case 11 * 4 + 1: ok = run_unit<11, 1>(w, u, smem, s_phase, setup); break;
         case 11 * 4 + 2: ok = run_unit<11, 2>(w, u, smem, s_phase, setup); break;
+        case 11 * 4 + 3: ok = run_unit<11, 3>(w, u, smem, s_phase, setup); break;
         case 12 * 4 + 0: ok = run_unit<12, 0>(w, u, smem, s_phase, setup); break;
         case 12 * 4 + 1: ok = run_unit<12, 1>(w, u, smem, s_phase, setup); break;
         case 12 * 4 + 2: ok = run_unit<12, 2>(w, u, smem, s_phase, setup); break;
+        case 12 * 4 + 3: ok = run_unit<12, 3>(w, u, smem, s_phase, setup); break;
         case 13 * 4 + 0: ok = run_unit<13, 0>(w, u, smem, s_phase, setup); break;
         case 13 * 4 + 1: ok = run_unit<13, 1>(w, u, smem, s_phase, setup); break;
         case 13 * 4 + 2: ok = run_unit<13, 2>(w, u, smem, s_phase, setup); break;
+        case 13 * 4 + 3: ok = run_unit<13, 3>(w, u, smem, s_phase, setup); break;
         case 14 * 4 + 0: ok = run_unit<14, 0>(w, u, smem, s_phase, setup); break;
         case 14 * 4 + 1: ok = run_unit<14, 1>(w, u, smem, s_phase, setup); break;
         case 14 * 4 + 2: ok = run_unit<14, 2>(w, u, smem, s_phase, setup); break;
+        case 14 * 4 + 3: ok = run_unit<14, 3>(w, u, smem, s_phase, setup); break;
         default: break;
         }
         prev_key = key;
@@ -167,7 +178,7 @@ struct isr_batch {
     int* counter = nullptr;
     int* status = nullptr;
     int order[4] = {0, 0, 0, 0};
-    float tune_ms[4][3] = {};
+    float tune_ms[4][4] = {};
     int64_t transforms = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -430,7 +441,7 @@ isr_status isr_batch_query(const isr_batch* b, isr_batch_info* info)
     info->transforms = b->transforms;
     for (int i = 0; i < 4; ++i) {
         info->order[i] = b->order[i];
-        for (int o = 0; o < 3; ++o) info->tune_ms[i][o] = b->tune_ms[i][o];
+        for (int o = 0; o < 4; ++o) info->tune_ms[i][o] = b->tune_ms[i][o];
     }
     return ISR_OK;
 }

@@ -42,7 +42,7 @@ __host__ __device__ constexpr int radix_of(int log2n, int order, int p)
     constexpr int t14[3][3] = {{32, 32, 16}, {16, 32, 32}, {32, 16, 32}};
     return log2n == 11 ? t11[order][p] : log2n == 12 ? t12[order][p] : log2n == 13 ? t13[order][p] : t14[order][p];
 }
-constexpr int kOrders = 3;
+constexpr int kOrders = 4;   // 0..2 Stockham orders, 3 the warp-local schedule
 
 template <int LOG2N, int ORDER = 0>
 struct Sched {
@@ -63,8 +63,9 @@ struct Sched {
     // passes build w^k by recurrence from a per-thread base w kept in a slot table.
     __host__ __device__ static constexpr int ns(int p) { return p == 1 ? R0 : R0 * R1; }
     __host__ __device__ static constexpr bool tab(int p) { return ns(p) * (radix(p) - 1) <= 1024; }
-    static constexpr int TAB1 = (NP > 1 && tab(1)) ? ns(1) * (R1 - 1) : 0;   // entries
-    static constexpr int TAB2 = (NP > 2 && tab(2)) ? ns(2) * (R2 - 1) : 0;
+    // table entries (float2), stored as pairs (w^{2p+1}, w^{2p+2}) in float4 [p][j mod Ns]
+    static constexpr int TAB1 = (NP > 1 && tab(1)) ? ns(1) * R1 : 0;
+    static constexpr int TAB2 = (NP > 2 && tab(2)) ? ns(2) * R2 : 0;
     static constexpr int SLOTS1 = (NP > 1 && !tab(1)) ? E / R1 : 0;           // per-thread bases
     static constexpr int SLOTS2 = (NP > 2 && !tab(2)) ? E / R2 : 0;
     static constexpr int NSLOT = SLOTS1 + SLOTS2;
@@ -243,14 +244,17 @@ __device__ __forceinline__ void twiddle(float2* v, float2 w)
     });
 }
 
-// apply w^k = tab[(k - 1) * NS + jm] (k = 1..R-1) to v[0..R)
+// apply w^k (k = 1..R-1) from a pair table: float4 [p][jm] = (w^{2p+1}, w^{2p+2}); one
+// 16-byte load brings two twiddles
 template <int R, int NS>
 __device__ __forceinline__ void twiddle_tab(float2* v, const float2* tab, int jm)
 {
-    const float2* t = tab + jm;
-    static_for<R - 1>([&](auto Kc) {
-        constexpr int k = decltype(Kc)::value + 1;
-        v[k] = cmul(v[k], t[(k - 1) * NS]);
+    const float4* t = reinterpret_cast<const float4*>(tab) + jm;
+    static_for<R / 2>([&](auto Pc) {
+        constexpr int pr = decltype(Pc)::value;
+        const float4 e = t[pr * NS];
+        v[2 * pr + 1] = cmul(v[2 * pr + 1], make_float2(e.x, e.y));
+        if constexpr (2 * pr + 2 < R) v[2 * pr + 2] = cmul(v[2 * pr + 2], make_float2(e.z, e.w));
     });
 }
 
@@ -318,7 +322,7 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
     // the previous unit of this CTA may still read the tables and the exchange buffer
     if (setup) __syncthreads();
     // per-thread twiddle bases of the recurrence passes, slot-major: [slot][t]
-    for (int i = tid; i < (setup ? S::NSLOT * T : 0); i += kThreads) {
+    for (int i = setup ? tid : S::NSLOT * T; i < S::NSLOT * T; i += kThreads) {
         int slot = i / T, tt = i - slot * T;
         int pass = slot < S::SLOTS1 ? 1 : 2;
         int b = pass == 1 ? slot : slot - S::SLOTS1;
@@ -331,14 +335,16 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
     if constexpr (P0 != P0_SIMT) {
         if (setup) tc_setup_afrags<P0>(afrag);
     }
-    // twiddle tables of the small passes: [k - 1][jm] = exp(-2 pi i jm k / (Ns R))
-    for (int i = tid; i < (setup ? S::TAB1 + S::TAB2 : 0); i += kThreads) {
+    // twiddle tables of the small passes: float4 [p][jm] = (w^{2p+1}, w^{2p+2}),
+    // w^k = exp(-2 pi i jm k / (Ns R))
+    for (int i = setup ? tid : S::TAB1 + S::TAB2; i < S::TAB1 + S::TAB2; i += kThreads) {
         int pass = i < S::TAB1 ? 1 : 2;
         int e = pass == 1 ? i : i - S::TAB1;
         int ns = S::ns(pass), R = S::radix(pass);
-        int k = e / ns + 1, jm = e - (k - 1) * ns;
-        double sn, cs;
-        sincospi(-2.0 * (double)(jm * k) / (double)(ns * R), &sn, &cs);
+        int e4 = e >> 1, pr = e4 / ns, jm = e4 - pr * ns;
+        int k = 2 * pr + 1 + (e & 1);
+        double sn = 0.0, cs = 0.0;
+        if (k < R) sincospi(-2.0 * (double)(jm * k) / (double)(ns * R), &sn, &cs);
         tab[i] = make_float2((float)cs, (float)sn);
     }
     __syncthreads();
@@ -477,6 +483,208 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
         });
     }
     return true;
+}
+
+// ---------------------------------------------------------------- warp-local schedule
+// Radix order 3 of nfft = M x 1024 (M = 2, 4, 8, 16): a decimation-in-frequency first pass,
+//   Z_q[n] = W_N^{n q} sum_{k<M} x[n + 1024 k] W_M^{k q}      (n < 1024, q < M),
+// spread over the gate's 32 M threads, then M independent 1024-point transforms,
+//   X[q + M m] = sum_n Z_q[n] W_1024^{n m},
+// one per warp, as a two-pass radix-32 Stockham FFT inside the warp.  Only the first pass
+// needs the whole gate's data, so an IPP takes two CTA barriers instead of four and the
+// warps run the rest independently.
+template <int LOG2N>
+struct SchedWL {
+    static constexpr int N = 1 << LOG2N;
+    static constexpr int M = N / 1024;          // first-pass radix = warps per gate
+    static constexpr int T = N / 32;            // threads per gate
+    static constexpr int G = kThreads / T;      // gates per CTA
+    static constexpr int BF = 32 / M;           // first-pass butterflies per thread
+    static constexpr int RPAD = 1024 + 64;      // one region (padded 2 per 32: 16-byte pairs)
+    static constexpr int STAGE_WORDS = Sched<LOG2N>::STAGE_WORDS;
+    static constexpr int OFF_MBAR = 0;
+    static constexpr int OFF_TWB = 64;                        // [b][t] bases W_N^n (per CTA)
+    static constexpr int OFF_TABC = OFF_TWB + 8 * 1024;       // float4 [p][l] (W^{(2p+1) l}, W^{(2p+2) l})
+    static constexpr int OFF_STAGE = OFF_TABC + 8 * 32 * 32;
+    static constexpr int OFF_REG = OFF_STAGE + 4 * STAGE_WORDS * G;
+    static constexpr int SMEM = OFF_REG + 8 * RPAD * M * G;
+    static_assert(LOG2N >= 11 && LOG2N <= 14, "warp-local schedule covers nfft 2048 .. 16384");
+};
+
+// two pad elements per 32 keep even elements 16-byte aligned for paired stores
+__device__ __forceinline__ int pid32(int i) { return i + 2 * (i >> 5); }
+
+template <int LOG2N, int TXT, bool FULL>
+__device__ __forceinline__ bool integrate_unit_wl(const KArgs a, const int gx, const int c, unsigned char* smem,
+                                                  const uint32_t phase0, const bool setup)
+{
+    using S = SchedWL<LOG2N>;
+    constexpr int N = S::N, M = S::M, T = S::T, G = S::G, BF = S::BF;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
+    float2* twb = reinterpret_cast<float2*>(smem + S::OFF_TWB);
+    float2* tabc = reinterpret_cast<float2*>(smem + S::OFF_TABC);
+
+    const int tid = threadIdx.x;
+    const int g = tid / T;
+    const int t = tid - g * T;
+    const int lane = t & 31, wg = t >> 5;
+    const int r = gx * G + g;
+    const bool valid = r < a.n_ranges;
+    const int64_t s_r = (int64_t)a.range_start + (int64_t)(valid ? r : a.n_ranges - 1) * a.range_step;
+    const int p_begin = c * a.chunk_len;
+    const int p_end = min(p_begin + a.chunk_len, a.n_ipp);
+    uint32_t* stage = reinterpret_cast<uint32_t*>(smem + S::OFF_STAGE) + g * S::STAGE_WORDS;
+    float2* reg = reinterpret_cast<float2*>(smem + S::OFF_REG) + g * M * S::RPAD;
+    const uint32_t bar = smem_u32(&mbar[g]);
+    const int off = (int)(s_r & 3);
+    const uint32_t copy_bytes = (uint32_t)(((off + a.code_len + 3) & ~3) * 4);
+    auto issue = [&](int p) {
+        const uint32_t* src = a.echo + (int64_t)p * a.echo_stride + (s_r - off);
+        bulk_load(smem_u32(stage), src, copy_bytes, bar);
+    };
+
+    if (setup) __syncthreads();
+    for (int i = setup ? tid : 1024; i < 1024; i += kThreads) {   // bases W_N^n, slot [b][t]
+        const int b = i / T, tt = i - b * T;
+        const int n = 2 * (tt + T * (b >> 1)) + (b & 1);
+        double sn, cs;
+        sincospi(-2.0 * (double)n / (double)N, &sn, &cs);
+        twb[i] = make_float2((float)cs, (float)sn);
+    }
+    for (int i = setup ? tid : 32 * 32; i < 32 * 32; i += kThreads) {
+        const int e4 = i >> 1, pr = e4 / 32, l = e4 % 32, k = 2 * pr + 1 + (i & 1);
+        double sn = 0.0, cs = 0.0;
+        if (k < 32) sincospi(-2.0 * (double)(l * k) / 1024.0, &sn, &cs);
+        tabc[i] = make_float2((float)cs, (float)sn);
+    }
+    __syncthreads();
+    if (t == 0 && p_begin < p_end && p_begin != a.drop_ipp) issue(p_begin);
+
+    const char* txbase = reinterpret_cast<const char*>(a.tx);
+    constexpr int CHIP = TXT == TX_CI16 ? 4 : TXT == TX_C32 ? 8 : 1;
+    // first-pass chips of this thread: bit b M + k for position n + 1024 k,
+    // n = 2 (t + T (b / 2)) + b % 2
+    auto signs_of = [&](const int8_t* row) {
+        uint32_t m = 0;
+        static_for<BF>([&](auto Bc) {
+            constexpr int b = decltype(Bc)::value;
+            static_for<M>([&](auto Kc) {
+                constexpr int k = decltype(Kc)::value;
+                const int pos = 2 * (t + T * (b >> 1)) + (b & 1) + 1024 * k;
+                if (pos < a.code_len && row[pos] < 0) m |= 1u << (b * M + k);
+            });
+        });
+        return m;
+    };
+    uint32_t signs = 0;
+    if constexpr (TXT == TX_PM1) {
+        if (a.tx_stride == 0) signs = signs_of(reinterpret_cast<const int8_t*>(txbase));
+    }
+
+    float acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+    float2 v[32];
+    bool timed_out = false;
+    int it = 0;
+    for (int p = p_begin; p < p_end; ++p, ++it) {
+        const bool ok = mbar_wait(bar, (phase0 + (uint32_t)it) & 1u, a.wait_limit);
+        // also orders the previous IPP's last reads of the regions before this IPP's writes
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        const char* txrow = txbase + (size_t)p * (size_t)a.tx_stride * CHIP;
+        if constexpr (TXT == TX_PM1) {
+            if (a.tx_stride != 0) signs = signs_of(reinterpret_cast<const int8_t*>(txrow));
+        }
+        // ---- pass A: decode, radix-M DFT over stride 1024, DIF twiddles, scatter to regions;
+        // butterflies b and b + 1 of a thread are the adjacent columns n, n + 1
+        float2 zp[M];
+        static_for<BF>([&](auto Bc) {
+            constexpr int b = decltype(Bc)::value;
+            const int n = 2 * (t + T * (b >> 1)) + (b & 1);
+            float2 u[M];
+            static_for<M>([&](auto Kc) {
+                constexpr int k = decltype(Kc)::value;
+                const int pos = n + 1024 * k;
+                u[k] = make_float2(0.f, 0.f);
+                if (FULL || pos < a.code_len)
+                    u[k] = decode<TXT>(stage[off + pos], txrow, pos, (signs << (31 - (b * M + k))) & 0x80000000u);
+            });
+            dft<M>(u);
+            const float2 w = twb[b * T + t];
+            float2 cur = w;
+            static_for<M>([&](auto Qc) {
+                constexpr int q = decltype(Qc)::value;
+                float2 z = u[BitRev<M>::at(q)];
+                if constexpr (q > 0) {
+                    z = cmul(z, cur);
+                    if constexpr (q + 1 < M) cur = cmul(cur, w);
+                }
+                if constexpr (b & 1) {
+                    *reinterpret_cast<float4*>(&reg[q * S::RPAD + pid32(n - 1)]) =
+                        make_float4(zp[q].x, zp[q].y, z.x, z.y);
+                } else {
+                    zp[q] = z;
+                }
+            });
+        });
+        __syncthreads();   // regions complete; the window is consumed
+        if (t == 0 && p + 1 < p_end && p + 1 != a.drop_ipp) {
+            fence_proxy_async();
+            issue(p + 1);
+        }
+        // ---- pass B (warp wg, region wg): radix-32 over stride 32, Stockham Ns = 1, in place
+        float2* rw = reg + wg * S::RPAD;
+        static_for<32>([&](auto Kc) {                       // rw[pid32(l + 32 k)] = rw[l + 34 k]
+            constexpr int k = decltype(Kc)::value;
+            v[k] = rw[lane + 34 * k];
+        });
+        dft<32>(v);
+        __syncwarp();
+        static_for<16>([&](auto Qc) {                       // y[32 l + q], q pairs: rw[34 l + q]
+            constexpr int q = 2 * decltype(Qc)::value;
+            const float2 x0 = v[BitRev<32>::at(q)], x1 = v[BitRev<32>::at(q + 1)];
+            *reinterpret_cast<float4*>(&rw[34 * lane + q]) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        });
+        __syncwarp();
+        // ---- pass C: twiddle W_1024^{l k}, radix-32, accumulate |X|^2 (bin wg + M (l + 32 q))
+        static_for<32>([&](auto Kc) {
+            constexpr int k = decltype(Kc)::value;
+            v[k] = rw[lane + 34 * k];
+        });
+        twiddle_tab<32, 32>(v, tabc, lane);
+        dft<32>(v);
+        static_for<32>([&](auto Qc) {
+            constexpr int q = decltype(Qc)::value;
+            const float2 X = v[BitRev<32>::at(q)];
+            acc[q] = fmaf(X.x, X.x, fmaf(X.y, X.y, acc[q]));
+        });
+    }
+
+    if (timed_out) {
+        if (tid == 0) atomicOr(a.status, 1);
+        mbar_wait(bar, (phase0 + (uint32_t)it) & 1u, a.wait_limit);
+        return false;
+    }
+    if (valid) {
+        float* out = a.partial + ((int64_t)c * a.n_ranges + r) * N;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) out[wg + M * (lane + 32 * q)] = acc[q];
+    }
+    return true;
+}
+
+template <int LOG2N, int TXT, bool FULL>
+__global__ void __launch_bounds__(kThreads, 1) integrate_kernel_wl(KArgs a)
+{
+    using S = SchedWL<LOG2N>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
+    if (threadIdx.x < S::G) mbar_init(smem_u32(&mbar[threadIdx.x]), 1);
+    fence_barrier_init();
+    integrate_unit_wl<LOG2N, TXT, FULL>(a, blockIdx.x, blockIdx.y, smem, 0u, true);
 }
 
 // One-shot launch: grid = (gate groups, IPP chunks), one unit per CTA.

@@ -123,7 +123,7 @@ class IsrBatchInfo(ctypes.Structure):
         ("n_units", ctypes.c_int64),
         ("transforms", ctypes.c_int64),
         ("order", ctypes.c_int32 * 4),
-        ("tune_ms", (ctypes.c_float * 3) * 4),
+        ("tune_ms", (ctypes.c_float * 4) * 4),
     ]
 
     def as_dict(self):
@@ -406,7 +406,8 @@ class Plan:
                        max_chunks=self.desc.max_chunks, device=self.desc.device, stream=self.desc.stream)
         times = []
         try:
-            for order in range(3):
+            n_orders = 5 if (self.desc.nfft == 16384 and self.desc.tx_type == ISR_TX_PM1) else 4
+            for order in range(n_orders):
                 isr_plan_set_order(scratch.handle, order)
                 scratch.integrate(echo, tx_code, n_ipp)   # warm-up
                 isr_spectra(scratch.handle, None, ISR_RESET_AFTER)
@@ -419,7 +420,7 @@ class Plan:
                 times.append(e0.elapsed_time(e1) / reps)
         finally:
             scratch.close()
-        best = int(min(range(3), key=lambda o: times[o]))
+        best = int(min(range(len(times)), key=lambda o: times[o]))
         isr_plan_set_order(self.handle, best)
         return {"order": best, "ms": times}
 

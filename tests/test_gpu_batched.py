@@ -24,7 +24,7 @@ def reference(bufs):
     return [o.cpu().numpy().astype(np.float64) for o in outs]
 
 
-@pytest.mark.parametrize("order", [0, 1, 2])
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
 def test_every_radix_order_matches_per_window_plans(bufs, reference, order):
     b = batched.Batch(bufs, flags=0, order=order)
     b.run()
@@ -40,7 +40,7 @@ def test_graph_replay_and_autotune(bufs, reference):
     used = {w.nfft for w in bufs.w}
     for k, n in enumerate(batched.NFFTS):
         if n in used:
-            assert info["order"][k] in (0, 1, 2) and min(info["tune_ms"][k]) > 0
+            assert info["order"][k] in (0, 1, 2, 3) and min(info["tune_ms"][k]) > 0
     b.run()
     first = [o.clone() for o in bufs.out]
     b.run()
