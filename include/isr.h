@@ -140,11 +140,13 @@ isr_status isr_plan_set_profiling(isr_plan* plan, int32_t enable);
  * and return; the next isr_spectra reports ISR_ERR_TIMEOUT.  polls must be > 0. */
 isr_status isr_plan_set_wait_limit(isr_plan* plan, uint32_t polls);
 
-/* Radix order (0..4) of the kernel used for binary-phase codes with code_len == nfft, for
+/* Radix order (0..5) of the kernel used for binary-phase codes with code_len == nfft, for
  * nfft >= 2048 (smaller sizes have one order): 0..2 are three-pass Stockham orders, 3 is a
  * radix-(nfft/1024) decimation-in-frequency pass followed by one 1024-point transform per
- * warp, 4 (nfft 16384 only) the passes [4, 16, 16, 16] with each thread transforming two
- * butterflies per paired FP32 instruction.  Every order gives
+ * warp; 4 and 5 (nfft 16384 only) use paired FP32 instructions (two operations each):
+ * 4 the passes [4, 16, 16, 16] with each thread transforming two butterflies at once,
+ * 5 the passes [16, 32, 32] of order 1 with two butterflies per thread in the first pass
+ * and each radix-32 butterfly split into two paired 16-point halves.  Every order gives
  * the same spectra up to FP32 rounding; they differ in speed, so a caller (or the
  * binding's autotuner) may time them and keep the fastest.  Default 0. */
 isr_status isr_plan_set_order(isr_plan* plan, int32_t order);

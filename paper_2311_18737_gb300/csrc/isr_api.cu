@@ -369,7 +369,7 @@ isr_status isr_plan_create(isr_plan** out, const isr_plan_desc* desc)
     if (p->ke.smem > smem_optin)
         return bail(fail(ISR_ERR_UNSUPPORTED, "kernel needs %d B shared memory, device allows %d", p->ke.smem, smem_optin));
     e = cudaFuncSetAttribute(p->ke.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->ke.smem);
-    for (int o = 0; o < 5 && e == cudaSuccess; ++o)
+    for (int o = 0; o < 6 && e == cudaSuccess; ++o)
         e = cudaFuncSetAttribute(p->ke.fn_order[o], cudaFuncAttributeMaxDynamicSharedMemorySize, p->ke.smem_order[o]);
     if (e != cudaSuccess) return bail(fail(ISR_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
 
@@ -501,10 +501,10 @@ isr_status isr_plan_set_wait_limit(isr_plan* p, uint32_t polls)
 
 isr_status isr_plan_set_order(isr_plan* p, int32_t order)
 {
-    if (!p || order < 0 || order > 4) return fail(ISR_ERR_INVALID_ARG, "plan is NULL or order not in 0..4");
+    if (!p || order < 0 || order > 5) return fail(ISR_ERR_INVALID_ARG, "plan is NULL or order not in 0..5");
     if (p->d.nfft < 2048 && order != 0) return fail(ISR_ERR_UNSUPPORTED, "radix orders exist for nfft >= 2048 only");
-    if (order == 4 && (p->d.nfft != 16384 || p->d.tx_type != ISR_TX_PM1))
-        return fail(ISR_ERR_UNSUPPORTED, "radix order 4 (paired) exists for nfft 16384 with ISR_TX_PM1 only");
+    if (order >= 4 && (p->d.nfft != 16384 || p->d.tx_type != ISR_TX_PM1))
+        return fail(ISR_ERR_UNSUPPORTED, "radix orders 4 and 5 (paired) exist for nfft 16384 with ISR_TX_PM1 only");
     p->order = order;
     return ISR_OK;
 }

@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(isr::kThreads, 1) batch_kernel(const BatchWin*
         default: break;
         }
         prev_key = key;
-        __syncthreads();
+        // gates sync on their own barriers inside a unit: agree on the outcome CTA-wide
+        const bool all_ok = __syncthreads_and(ok) != 0;
         if (threadIdx.x == 0) {
             // every gate-group slot of this shape completed one phase per IPP of the unit
             const int G = isr::kThreads / (1 << (w.log2n - 5));
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(isr::kThreads, 1) batch_kernel(const BatchWin*
             const int n = min(p0 + w.a.chunk_len, w.a.n_ipp) - p0;
             for (int g = 0; g < G; ++g) s_phase[g] += (uint32_t)n;
         }
-        if (!ok) break;   // a wait ran out: the status word is set, stop pulling work
+        if (!all_ok) break;   // a wait ran out: the status word is set, stop pulling work
     }
 }
 

@@ -275,7 +275,9 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
     constexpr int N = S::N, E = S::E, T = S::T, G = S::G, NP = S::NP;
     constexpr int R0 = S::R0;
     constexpr int RL = S::radix(NP - 1);  // radix of the last pass
-    // transforms of 32 or fewer threads live inside one warp and sync per warp
+    // transforms of 32 or fewer threads live inside one warp and sync per warp; with several
+    // gates per CTA each gate's threads sync on a named barrier of their own (1 + g), so the
+    // gates of a CTA run their passes independently and their FFT and exchange phases overlap
     constexpr bool CTA_SYNC = T > 32;
     static_assert(P0 == P0_SIMT || (LOG2N == 14 && ORDER == 1 && TXT == TX_PM1 && FULL),
                   "the tensor-core first pass exists for nfft 16384, radix order 1, full binary-phase codes");
@@ -288,6 +290,29 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
     const int g = tid / T;
     const int t = tid - g * T;
     const int r = gx * G + g;
+    auto gsync = [&]() {
+        if constexpr (!CTA_SYNC) __syncwarp();
+        else if constexpr (G == 1) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(T) : "memory");
+    };
+    auto gsync_or = [&](bool pred) -> bool {
+        if constexpr (!CTA_SYNC) {
+            return __any_sync(0xffffffffu, pred);
+        } else if constexpr (G == 1) {
+            return __syncthreads_or(pred) != 0;
+        } else {
+            uint32_t any;
+            asm volatile(
+                "{\n\t.reg .pred p, q;\n\t"
+                "setp.ne.u32 p, %1, 0;\n\t"
+                "bar.red.or.pred q, %2, %3, p;\n\t"
+                "selp.u32 %0, 1, 0, q;\n\t}"
+                : "=r"(any)
+                : "r"((uint32_t)pred), "r"(1 + g), "n"(T)
+                : "memory");
+            return any != 0;
+        }
+    };
     const bool valid = r < a.n_ranges;
     const int64_t s_r = (int64_t)a.range_start + (int64_t)(valid ? r : a.n_ranges - 1) * a.range_step;
     const int p_begin = c * a.chunk_len;
@@ -369,9 +394,9 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
     int it = 0;
     for (int p = p_begin; p < p_end; ++p, ++it) {
         const bool ok = mbar_wait(bar, (phase0 + (uint32_t)it) & 1u, a.wait_limit);
-        // every thread of the CTA agrees before anyone leaves; this barrier also orders the
+        // every thread of the gate agrees before anyone leaves; this barrier also orders the
         // previous IPP's last-pass reads of xch before this IPP's first-pass writes
-        const bool any_fail = CTA_SYNC ? __syncthreads_or(!ok) : __any_sync(0xffffffffu, !ok);
+        const bool any_fail = gsync_or(!ok);
         if (any_fail) {
             timed_out = true;
             break;
@@ -411,7 +436,7 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
         });
 
         // window fully consumed and first-pass outputs visible
-        if (CTA_SYNC) __syncthreads(); else __syncwarp();
+        gsync();
         if (t == 0 && p + 1 < p_end && p + 1 != a.drop_ipp) {
             fence_proxy_async();
             issue(p + 1);
@@ -430,14 +455,14 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
                 else twiddle<R>(u, twb[b * T + t]);
                 dft<R>(u);
             });
-            if (CTA_SYNC) __syncthreads(); else __syncwarp();
+            gsync();
             static_for<E / R>([&](auto Bc) {
                 constexpr int b = decltype(Bc)::value;
                 const int j = t + T * b;
                 const int idxD = (j / NS) * NS * R + (j % NS);
                 store_strided<NS, R, S::PADP>(xch, idxD, v + b * R);
             });
-            if (CTA_SYNC) __syncthreads(); else __syncwarp();
+            gsync();
         }
 
         // ---- last pass: read, twiddle, DFT, accumulate |X|^2 in registers
@@ -464,7 +489,7 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
     }
 
     if (timed_out) {
-        if (tid == 0) atomicOr(a.status, 1);
+        if (t == 0) atomicOr(a.status, 1);
         // let the copy still in flight land before the CTA's shared memory is released
         mbar_wait(bar, (phase0 + (uint32_t)it) & 1u, a.wait_limit);
         return false;

@@ -14,8 +14,8 @@ void clear_error();
 struct KernelEntry {
     const void* fn;   // __global__ integrate_kernel<LOG2N, TXT>
     const void* fn_full;  // the same for code_len == nfft (binary-phase codes only; else fn)
-    const void* fn_order[5];  // fn_full with radix order 0..4 (orders 1-3: nfft >= 2048, 4: 16384)
-    int smem_order[5];        // their shared memory
+    const void* fn_order[6];  // fn_full with radix order 0..5 (orders 1-3: nfft >= 2048, 4-5: 16384)
+    int smem_order[6];        // their shared memory
     const void* fn_tc[5];     // [mode] tensor-core first pass (nfft 16384, binary phase); [0] unused
     int smem_tc;
     int smem;         // dynamic shared memory bytes
@@ -31,7 +31,7 @@ KernelEntry entry_for(int txt)
                   : txt == TX_C32  ? (const void*)integrate_kernel<L, TX_C32>
                                    : (const void*)integrate_kernel<L, TX_PM1>;
     const void* ff = txt == TX_PM1 ? (const void*)integrate_kernel<L, TX_PM1, true> : f;
-    KernelEntry e{f, ff, {ff, ff, ff, ff, ff}, {S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM},
+    KernelEntry e{f, ff, {ff, ff, ff, ff, ff, ff}, {S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM},
                   {nullptr, nullptr, nullptr, nullptr, nullptr},
                   0, S::SMEM, S::G, kThreads};
     if constexpr (L >= 11) {
@@ -48,6 +48,8 @@ KernelEntry entry_for(int txt)
         if (txt == TX_PM1) {
             e.fn_order[4] = (const void*)integrate_kernel_p<true>;
             e.smem_order[4] = SchedP::SMEM;
+            e.fn_order[5] = (const void*)integrate_kernel_q<true>;
+            e.smem_order[5] = SchedQ::SMEM;
             e.fn_tc[1] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_BF16_SPLIT>;
             e.fn_tc[2] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_FP16_SPLIT>;
             e.fn_tc[3] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_BF16>;

@@ -340,4 +340,223 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel_p(KArgs a)
     integrate_unit_p<FULL>(a, blockIdx.x, blockIdx.y, smem, 0u, true);
 }
 
+// ---------------------------------------------------------------- paired schedule [16, 32, 32]
+// Radix order 5 (nfft 16384): the Stockham passes of radix order 1 with paired arithmetic.
+//  pass 0 (radix 16, Ns = 1): thread t transforms butterflies t and t + 512 as one CP
+//    stream.  Their outputs y[16 j + q] lie N/2 apart, so the first exchange layout keeps
+//    y[s] and y[s + N/2] in one 16-byte slot s < N/2, (re, re', im, im'): one 16-byte store
+//    per output pair.
+//  pass 1 (radix 32, Ns = 16) and pass 2 (radix 32, Ns = 512): butterfly t.  With input
+//    twiddles w^k the first radix-2 DIF stage of the 32-point DFT is
+//        A_k = w^k (x_k + w^16 x_{k+16}),   B_k = (w W_32)^k (x_k - w^16 x_{k+16}),  k < 16,
+//    computed as scalar FP32 for s_k = x_k + w^16 x_{k+16} and d_k = x_k - w^16 x_{k+16},
+//    then (s_k, d_k) times the twiddle pair (w^k, (w W_32)^k) as one CP; a paired 16-point
+//    DFT of (A, B) gives X[2u] (lane 0) and X[2u + 1] (lane 1).  Pass 1 reads its inputs
+//    k, k + 16 (N/2 apart) as one slot of the first layout and writes the plain padded
+//    complex layout of radix order 1, which pass 2 reads; pass 2 accumulates |X|^2 for
+//    the bin pair (2u, 2u + 1) in one paired register.
+struct SchedQ {
+    static constexpr int N = 16384;
+    static constexpr int SLOTS = N / 2 + N / 32;   // first layout: 16-byte slots, one pad per 16
+    static constexpr int NPAD = N + N / 16;        // second layout: float2, one pad per 16
+    static constexpr int OFF_MBAR = 0;
+    static constexpr int OFF_BASE = 64;                      // float4 [t]: (w, w W_32), w = W_N^t
+    static constexpr int OFF_W16 = OFF_BASE + 16 * 512;      // float2 [t]: W_1024^t (= w^16, pass 2)
+    static constexpr int OFF_TAB1 = OFF_W16 + 8 * 512;       // float4 [k - 1][jm], pass 1, k = 1..15
+    static constexpr int OFF_T16 = OFF_TAB1 + 16 * 15 * 16;  // float2 [jm]: W_32^jm (= w^16, pass 1)
+    static constexpr int OFF_STAGE = OFF_T16 + 8 * 16;
+    static constexpr int STAGE_WORDS = N + 4;
+    static constexpr int OFF_XCH = OFF_STAGE + 4 * STAGE_WORDS;
+    static constexpr int XCH_BYTES = 16 * SLOTS > 8 * NPAD ? 16 * SLOTS : 8 * NPAD;
+    static constexpr int SMEM = OFF_XCH + XCH_BYTES;
+    static_assert(OFF_STAGE % 16 == 0 && OFF_XCH % 16 == 0, "bulk copies and 16-byte slots need alignment");
+};
+
+// first exchange layout: slot s -> s + s / 16 (16-byte units)
+__device__ __forceinline__ int qslot(int s) { return s + (s >> 4); }
+
+// first DIF stage of a 32-point DFT for inputs a = x_k, b = x_{k+16} (scalar FP32):
+// (s, d) = (a + w16 b, a - w16 b) as one CP
+__device__ __forceinline__ CP dif_first(const float2 a, const float2 b, const float2 w16)
+{
+    const float2 y = cmul(b, w16);
+    return CP{make_float2(a.x + y.x, a.x - y.x), make_float2(a.y + y.y, a.y - y.y)};
+}
+
+template <bool FULL>
+__device__ __forceinline__ bool integrate_unit_q(const KArgs a, const int gx, const int c, unsigned char* smem,
+                                                 const uint32_t phase0, const bool setup)
+{
+    using S = SchedQ;
+    constexpr int N = S::N;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
+    float4* base = reinterpret_cast<float4*>(smem + S::OFF_BASE);
+    float2* w16t = reinterpret_cast<float2*>(smem + S::OFF_W16);
+    float4* tab1 = reinterpret_cast<float4*>(smem + S::OFF_TAB1);
+    float2* t16 = reinterpret_cast<float2*>(smem + S::OFF_T16);
+    uint32_t* stage = reinterpret_cast<uint32_t*>(smem + S::OFF_STAGE);
+    float4* x1 = reinterpret_cast<float4*>(smem + S::OFF_XCH);   // first layout
+    float2* x2 = reinterpret_cast<float2*>(smem + S::OFF_XCH);   // second layout
+
+    const int t = threadIdx.x;
+    const int r = gx;
+    const bool valid = r < a.n_ranges;
+    const int64_t s_r = (int64_t)a.range_start + (int64_t)(valid ? r : a.n_ranges - 1) * a.range_step;
+    const int p_begin = c * a.chunk_len;
+    const int p_end = min(p_begin + a.chunk_len, a.n_ipp);
+    const uint32_t bar = smem_u32(&mbar[0]);
+    const int off = (int)(s_r & 3);
+    const uint32_t copy_bytes = (uint32_t)(((off + a.code_len + 3) & ~3) * 4);
+    auto issue = [&](int p) {
+        const uint32_t* src = a.echo + (int64_t)p * a.echo_stride + (s_r - off);
+        bulk_load(smem_u32(stage), src, copy_bytes, bar);
+    };
+
+    if (setup) __syncthreads();
+    if (setup) {
+        base[t] = tw_pair(t, t + 512, N);                       // (w, w W_32), w = W_N^t
+        {
+            double sn, cs;
+            sincospi(-2.0 * (double)t / 1024.0, &sn, &cs);     // w^16 = W_1024^t
+            w16t[t] = make_float2((float)cs, (float)sn);
+        }
+        if (t < 15 * 16) {                                      // pass 1: w = W_512^jm
+            const int k = t / 16 + 1, jm = t % 16;
+            tab1[t] = tw_pair(jm * k, (jm + 16) * k, 512);     // (w^k, (w W_32)^k)
+        } else if (t < 15 * 16 + 16) {
+            const int jm = t - 15 * 16;
+            double sn, cs;
+            sincospi(-2.0 * (double)jm / 32.0, &sn, &cs);       // w^16 = W_32^jm
+            t16[jm] = make_float2((float)cs, (float)sn);
+        }
+    }
+    __syncthreads();
+    if (t == 0 && p_begin < p_end && p_begin != a.drop_ipp) issue(p_begin);
+
+    const int8_t* code = reinterpret_cast<const int8_t*>(a.tx);
+    // chips of pass 0: bit b * 16 + k for position t + 512 b + 1024 k (radix order 1's layout)
+    uint32_t signs = a.tx_stride == 0 ? load_signs<14, 1>(code, t, a.code_len) : 0u;
+
+    float2 acc[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc[u] = make_float2(0.f, 0.f);
+    const int jm = t & 15;
+    bool timed_out = false;
+    int it = 0;
+    for (int p = p_begin; p < p_end; ++p, ++it) {
+        const bool ok = mbar_wait(bar, (phase0 + (uint32_t)it) & 1u, a.wait_limit);
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        if (a.tx_stride != 0) signs = load_signs<14, 1>(code + (size_t)p * (size_t)a.tx_stride, t, a.code_len);
+
+        CP v[16];
+        // ---- pass 0: decode, two radix-16 butterflies (t, t + 512) in lock step
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            float2 rr, ii;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int pos = t + 512 * b + 1024 * k;
+                float2 z = make_float2(0.f, 0.f);
+                if (FULL || pos < a.code_len)
+                    z = decode<TX_PM1>(stage[off + pos], nullptr, pos, (signs << (31 - (b * 16 + k))) & 0x80000000u);
+                if (b == 0) {
+                    rr.x = z.x;
+                    ii.x = z.y;
+                } else {
+                    rr.y = z.x;
+                    ii.y = z.y;
+                }
+            }
+            v[k] = CP{rr, ii};
+        }
+        pdft16(v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) x1[qslot(16 * t) + q] = make_float4(v[q].re.x, v[q].re.y, v[q].im.x, v[q].im.y);
+        __syncthreads();   // pass-0 outputs complete; the window is consumed
+        if (t == 0 && p + 1 < p_end && p + 1 != a.drop_ipp) {
+            fence_proxy_async();
+            issue(p + 1);
+        }
+
+        // ---- pass 1: radix 32, Ns = 16, twiddles from the table
+        const float2 w16p1 = t16[jm];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float4 e = x1[qslot(t) + 544 * k];   // inputs k and k + 16
+            v[k] = dif_first(make_float2(e.x, e.z), make_float2(e.y, e.w), w16p1);
+        }
+#pragma unroll
+        for (int k = 1; k < 16; ++k) {
+            const float4 w = tab1[(k - 1) * 16 + jm];
+            const float2 wim = make_float2(w.z, w.w);
+            v[k] = pmul(v[k], make_float2(w.x, w.y), wim, __fmul2_rn(wim, bc(-1.f)));
+        }
+        pdft16(v);
+        __syncthreads();
+        {
+            // X[q] of butterfly t at (t / 16) 512 + t % 16 + 16 q, padded one per 16
+            float2* o = x2 + (t >> 4) * 544 + (t & 15);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                o[17 * (2 * u)] = make_float2(v[u].re.x, v[u].im.x);
+                o[17 * (2 * u + 1)] = make_float2(v[u].re.y, v[u].im.y);
+            }
+        }
+        __syncthreads();
+
+        // ---- pass 2: radix 32, Ns = 512, twiddles by a paired recurrence; accumulate |X|^2
+        {
+            const float2* in = x2 + t + (t >> 4);
+            const float2 w16p2 = w16t[t];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] = dif_first(in[544 * k], in[544 * (k + 16)], w16p2);
+            const float4 b2 = base[t];
+            const float2 c1re = make_float2(b2.x, b2.y), c1im = make_float2(b2.z, b2.w);
+            const float2 c1nim = __fmul2_rn(c1im, bc(-1.f));
+            float2 cre = c1re, cim = c1im;
+#pragma unroll
+            for (int k = 1; k < 16; ++k) {
+                v[k] = pmul(v[k], cre, cim, __fmul2_rn(cim, bc(-1.f)));
+                if (k < 15) {
+                    const CP nc = pmul(CP{cre, cim}, c1re, c1im, c1nim);
+                    cre = nc.re;
+                    cim = nc.im;
+                }
+            }
+        }
+        pdft16(v);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc[u] = __ffma2_rn(v[u].im, v[u].im, __ffma2_rn(v[u].re, v[u].re, acc[u]));
+    }
+
+    if (timed_out) {
+        if (t == 0) atomicOr(a.status, 1);
+        mbar_wait(bar, (phase0 + (uint32_t)it) & 1u, a.wait_limit);
+        return false;
+    }
+    // bins t + 512 q: acc[u] holds q = 2u (x) and q = 2u + 1 (y)
+    if (valid) {
+        float* out = a.partial + ((int64_t)c * a.n_ranges + r) * N;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            out[t + 1024 * u] = acc[u].x;
+            out[t + 1024 * u + 512] = acc[u].y;
+        }
+    }
+    return true;
+}
+
+template <bool FULL>
+__global__ void __launch_bounds__(kThreads, 1) integrate_kernel_q(KArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
+    if (threadIdx.x == 0) mbar_init(smem_u32(&mbar[0]), 1);
+    fence_barrier_init();
+    integrate_unit_q<FULL>(a, blockIdx.x, blockIdx.y, smem, 0u, true);
+}
+
 }  // namespace isr

@@ -406,7 +406,7 @@ class Plan:
                        max_chunks=self.desc.max_chunks, device=self.desc.device, stream=self.desc.stream)
         times = []
         try:
-            n_orders = 5 if (self.desc.nfft == 16384 and self.desc.tx_type == ISR_TX_PM1) else 4
+            n_orders = 6 if (self.desc.nfft == 16384 and self.desc.tx_type == ISR_TX_PM1) else 4
             for order in range(n_orders):
                 isr_plan_set_order(scratch.handle, order)
                 scratch.integrate(echo, tx_code, n_ipp)   # warm-up
