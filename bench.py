@@ -31,6 +31,9 @@ if ROOT not in sys.path:
 METRIC = "range-gate spectra/sec (nfft=16384)"
 UNIT = "spectra/s"
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
+# sources that define the fused kernel and its launch (the recorded DRAM traffic is tied to them)
+TRAFFIC_SOURCES = ("isr_fft.cuh", "isr_kernel.cuh", "isr_tc.cuh", "isr_paired.cuh", "isr_kernels.cuh",
+                   "isr_k_16384.cu", "isr_api.cu")
 
 
 def _peaks():
@@ -296,7 +299,15 @@ def run_ours(args):
     flops_per_transform = 5.0 * N * math.log2(N)
     transforms_per_launch = R * P / max(1.0, launches_per_step)
     achieved = flops_per_transform * transforms_per_launch / (kernel_ms / 1000) / 1e12 if kernel_ms > 0 else None
-    traffic = _recorded_traffic(N)
+    traffic = _recorded_traffic(N, R, P, tune["order"])
+    # measured FP32 FMA rate (own microkernel, after the timed region): cross-check of the derived peak
+    measured = None
+    if not args.no_peak:
+        ffma, _ = isr.isr_fp32_peak(local, False)
+        ffma2, _ = isr.isr_fp32_peak(local, True)
+        measured = {"ffma": ffma, "ffma2": ffma2, "unit": "TFLOP/s",
+                    "how": "isr_fp32_peak: FMA-only kernel, 8 independent chains per thread, 4 x 256 threads "
+                           "per SM, best of 3 runs; ffma2 = paired FP32 instruction"}
 
     line = {"metric": METRIC, "value": job_throughput(world, R, P, ms), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
@@ -312,7 +323,12 @@ def run_ours(args):
                          "frac": (achieved / fp32_peak_tflops) if achieved else None, "traffic": traffic,
                          "peak_basis": "derived FP32 SIMT peak: %d SMs x %d lanes x 2 FLOP x %.0f MHz (sm max)"
                                        % (props.multi_processor_count, FP32_LANES_PER_SM, sm_max),
-                         "flop_model": "5 N log2 N per transform", "kernel_ms_per_launch": kernel_ms},
+                         "flop_model": "5 N log2 N per transform", "kernel_ms_per_launch": kernel_ms,
+                         "peak_measured": measured,
+                         "hbm_gbs": (traffic / (kernel_ms / 1000) / 1e9) if (traffic and kernel_ms > 0) else None,
+                         "hbm_frac_of_measured": (traffic / (kernel_ms / 1000) / 1e9 / peaks["hbm_gbs"])
+                         if (traffic and kernel_ms > 0 and peaks.get("hbm_gbs")) else None,
+                         "frac_of_measured": (achieved / measured["ffma"]) if (achieved and measured) else None},
             "clocks": clocks, "e2e": e2e}
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -329,9 +345,9 @@ def run_ours(args):
     return 0
 
 
-def _recorded_traffic(nfft):
+def _recorded_traffic(nfft, n_ranges, n_ipp, order):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (else null)."""
+    current kernel source, the same workload shape and radix order (else null)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -341,11 +357,12 @@ def _recorded_traffic(nfft):
         return None
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2311_18737_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     if rec.get("kernel_source_sha256") != h.hexdigest():
+        return None
+    if rec.get("workload") != {"n_ranges": n_ranges, "n_ipp": n_ipp} or rec.get("radix_order") != order:
         return None
     return rec.get("bytes_per_launch", {}).get(str(nfft))
 
@@ -362,6 +379,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--order", type=int, default=None, help="force a radix order (no autotuning)")
+    ap.add_argument("--no-peak", action="store_true", help="skip the FP32 FMA-rate microkernel")
     ap.add_argument("--ref-gates", type=int, default=256)
     ap.add_argument("--ref-ipps", type=int, default=256)
     ap.add_argument("--n-ranges", type=int, default=None, help="resize the workload (profiling cases)")

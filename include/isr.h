@@ -210,6 +210,19 @@ isr_status isr_peak_fit(const float* spectra, int32_t n_ranges, int32_t nfft, in
                         double* freq_bin, float* snr, void* stream);
 
 /*
+ * Measured FP32 fused multiply-add throughput of `device`: the denominator of the integrate
+ * kernel's roofline (the kernel is bound by the FP32 SIMT pipe, whose nominal rate is SMs x 128
+ * lanes x 2 FLOP x SM clock).  An FMA-only kernel (8 independent dependency chains per thread,
+ * 4 CTAs of 256 threads per SM) runs 4 times on an internal stream; the best of runs 2-4 is
+ * reported.  paired = 0 issues FFMA (one FMA per lane and instruction), paired = 1 FFMA2 (two
+ * per lane and instruction).  Writes *tflops (2 FLOP per FMA) and *ms (duration of the best
+ * run).  Blocking; allocates 4 bytes of device memory for the duration of the call.  The paper
+ * has no counterpart.  Errors: ISR_ERR_INVALID_ARG (NULL output, paired not 0/1; checked before
+ * any CUDA call), ISR_ERR_CUDA.
+ */
+isr_status isr_fp32_peak(int32_t device, int32_t paired, double* tflops, double* ms);
+
+/*
  * Learned plasma-line estimator (the network maps an integrated spectrum to the line's
  * position and presence; Eq. 1 links that position to the electron density).  Network:
  * four 9-tap, 32-channel 1-D convolutions with ReLU over the band's standardised log

@@ -17,7 +17,7 @@ OBJDIR = os.path.join(LIBDIR, "obj")
 LIB = os.path.join(LIBDIR, "libisr.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-UNITS = ["isr_api.cu", "isr_linefit.cu", "isr_estimator.cu", "isr_batch.cu", "isr_k_small.cu", "isr_k_mid.cu", "isr_k_8192.cu", "isr_k_16384.cu"]
+UNITS = ["isr_api.cu", "isr_linefit.cu", "isr_peak.cu", "isr_estimator.cu", "isr_batch.cu", "isr_k_small.cu", "isr_k_mid.cu", "isr_k_8192.cu", "isr_k_16384.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", f"-I{INCLUDE}", f"-I{CSRC}"]
 

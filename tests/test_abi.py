@@ -71,3 +71,10 @@ def test_null_arguments():
     assert lib.isr_integrate(None, None, None, 1, None, 1024) == isr.ISR_ERR_INVALID_ARG
     assert lib.isr_spectra(None, None, 0, None) == isr.ISR_ERR_INVALID_ARG
     lib.isr_destroy(None)  # NULL is safe
+
+
+def test_fp32_peak_rejects_bad_arguments_on_host():
+    lib = isr.load_library()
+    assert lib.isr_fp32_peak(0, 0, None, None) == isr.ISR_ERR_INVALID_ARG
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    assert lib.isr_fp32_peak(0, 2, ctypes.byref(tf), ctypes.byref(ms)) == isr.ISR_ERR_INVALID_ARG
