@@ -173,6 +173,21 @@ def _cpu_sample(w, n_gates, n_ipp, threads):
     return len(sel) * n_ipp / dt, len(sel), dt
 
 
+def _numpy_sample(w, n_gates, n_ipp):
+    """Time the paper-style NumPy implementation (the paper's CPU comparison: per IPP a decoded
+    batch, numpy.fft.fft per row, |X|^2 added; one core) on n_gates gates x n_ipp IPPs."""
+    import numpy as np
+
+    from oracle import numpy_paper
+    echo = w.echo_host(0, n_ipp)
+    code = w.code()
+    sel = np.unique(np.linspace(0, w.n_ranges - 1, n_gates).astype(np.int64))
+    t0 = time.perf_counter()
+    numpy_paper.integrate(echo, code, w.nfft, w.n_ranges, w.range_start, w.range_step, gates=sel)
+    dt = time.perf_counter() - t0
+    return len(sel) * n_ipp / dt, len(sel), dt
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -336,6 +351,10 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"{ng} gates spread over the workload x the first {args.ref_ipps} IPPs "
                                           f"({dt:.1f} s wall)"}
+        v, ng, dt = _numpy_sample(w, 64, 32)
+        line["cpu_baseline_numpy"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "paper-style NumPy (Sec. 3.3)",
+                                      "sample": f"{ng} gates spread over the workload x the first 32 IPPs "
+                                                f"({dt:.1f} s wall)"}
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
