@@ -64,8 +64,11 @@ struct Sched {
     __host__ __device__ static constexpr int ns(int p) { return p == 1 ? R0 : R0 * R1; }
     __host__ __device__ static constexpr bool tab(int p) { return ns(p) * (radix(p) - 1) <= 1024; }
     // table entries (float2), stored as pairs (w^{2p+1}, w^{2p+2}) in float4 [p][j mod Ns]
-    static constexpr int TAB1 = (NP > 1 && tab(1)) ? ns(1) * R1 : 0;
-    static constexpr int TAB2 = (NP > 2 && tab(2)) ? ns(2) * R2 : 0;
+    // radix 16 and 32 keep only (w, w^2), (w^3, w^4), (w^8, w^16) per j mod Ns (6 entries) and
+    // form the other powers with one product each; smaller radices keep every power
+    __host__ __device__ static constexpr int tabw(int p) { return radix(p) >= 16 ? 6 : radix(p); }
+    static constexpr int TAB1 = (NP > 1 && tab(1)) ? ns(1) * tabw(1) : 0;
+    static constexpr int TAB2 = (NP > 2 && tab(2)) ? ns(2) * tabw(2) : 0;
     static constexpr int SLOTS1 = (NP > 1 && !tab(1)) ? E / R1 : 0;           // per-thread bases
     static constexpr int SLOTS2 = (NP > 2 && !tab(2)) ? E / R2 : 0;
     static constexpr int NSLOT = SLOTS1 + SLOTS2;
@@ -232,16 +235,54 @@ __device__ __forceinline__ uint32_t load_signs(const int8_t* row, int t, int cod
     return m;
 }
 
-// apply the Stockham twiddles w^k (k = 1..R-1) to v[0..R) given w
+// apply the Stockham twiddles w^k (k = 1..R-1) to v[0..R) given w.  Radix <= 8: a chain
+// w^{k+1} = w^k w.  Radix 16 and 32: the same R - 2 products arranged as a shallow tree,
+// w^2..w^7 from w, then w^{8 m + i} = w^{8 m} w^i with w^8 = (w^4)^2, w^16 = (w^8)^2 and
+// w^24 = w^16 w^8, so no power is more than six products from w.
 template <int R>
 __device__ __forceinline__ void twiddle(float2* v, float2 w)
 {
-    float2 cur = w;
-    static_for<R - 1>([&](auto Kc) {
-        constexpr int k = decltype(Kc)::value + 1;
-        v[k] = cmul(v[k], cur);
-        if constexpr (k + 1 < R) cur = cmul(cur, w);
-    });
+    if constexpr (R < 16) {
+        float2 cur = w;
+        static_for<R - 1>([&](auto Kc) {
+            constexpr int k = decltype(Kc)::value + 1;
+            v[k] = cmul(v[k], cur);
+            if constexpr (k + 1 < R) cur = cmul(cur, w);
+        });
+    } else {
+        float2 p[8];
+        p[1] = w;
+        p[2] = cmul(w, w);
+        p[3] = cmul(p[2], w);
+        p[4] = cmul(p[2], p[2]);
+        p[5] = cmul(p[4], w);
+        p[6] = cmul(p[4], p[2]);
+        p[7] = cmul(p[4], p[3]);
+        static_for<7>([&](auto Ic) {
+            constexpr int i = decltype(Ic)::value + 1;
+            v[i] = cmul(v[i], p[i]);
+        });
+        const float2 w8 = cmul(p[4], p[4]);
+        v[8] = cmul(v[8], w8);
+        static_for<7>([&](auto Ic) {
+            constexpr int i = decltype(Ic)::value + 1;
+            v[8 + i] = cmul(v[8 + i], cmul(w8, p[i]));
+        });
+        if constexpr (R == 32) {
+            const float2 w16 = cmul(w8, w8);
+            v[16] = cmul(v[16], w16);
+            static_for<7>([&](auto Ic) {
+                constexpr int i = decltype(Ic)::value + 1;
+                v[16 + i] = cmul(v[16 + i], cmul(w16, p[i]));
+            });
+            const float2 w24 = cmul(w16, w8);
+            v[24] = cmul(v[24], w24);
+            static_for<7>([&](auto Ic) {
+                constexpr int i = decltype(Ic)::value + 1;
+                v[24 + i] = cmul(v[24 + i], cmul(w24, p[i]));
+            });
+        }
+    }
 }
 
 // apply w^k (k = 1..R-1) from a pair table: float4 [p][jm] = (w^{2p+1}, w^{2p+2}); one
@@ -256,6 +297,49 @@ __device__ __forceinline__ void twiddle_tab(float2* v, const float2* tab, int jm
         v[2 * pr + 1] = cmul(v[2 * pr + 1], make_float2(e.x, e.y));
         if constexpr (2 * pr + 2 < R) v[2 * pr + 2] = cmul(v[2 * pr + 2], make_float2(e.z, e.w));
     });
+}
+
+// apply w^k (k = 1..R-1, R = 16 or 32) from three table pairs (w, w^2), (w^3, w^4), (w^8, w^16):
+// w^5..w^7 = w^4 w^{1..3}, w^{8+i} = w^8 w^i, w^{16+i} = w^16 w^i; every power is at most two
+// products from the table (error ~2 ulp), and the table costs 3 of the R/2 16-byte loads
+template <int R, int NS>
+__device__ __forceinline__ void twiddle_tab3(float2* v, const float2* tab, int jm)
+{
+    static_assert(R == 16 || R == 32, "three-pair table covers radix 16 and 32");
+    const float4* t = reinterpret_cast<const float4*>(tab) + jm;
+    const float4 a = t[0], b = t[NS], c = t[2 * NS];
+    float2 w[8];
+    w[1] = make_float2(a.x, a.y);
+    w[2] = make_float2(a.z, a.w);
+    w[3] = make_float2(b.x, b.y);
+    w[4] = make_float2(b.z, b.w);
+    w[5] = cmul(w[4], w[1]);
+    w[6] = cmul(w[4], w[2]);
+    w[7] = cmul(w[4], w[3]);
+    const float2 w8 = make_float2(c.x, c.y);
+    static_for<7>([&](auto Ic) {
+        constexpr int i = decltype(Ic)::value + 1;
+        v[i] = cmul(v[i], w[i]);
+    });
+    v[8] = cmul(v[8], w8);
+    static_for<7>([&](auto Ic) {
+        constexpr int i = decltype(Ic)::value + 1;
+        v[8 + i] = cmul(v[8 + i], cmul(w8, w[i]));
+    });
+    if constexpr (R == 32) {
+        const float2 w16 = make_float2(c.z, c.w);
+        v[16] = cmul(v[16], w16);
+        static_for<7>([&](auto Ic) {
+            constexpr int i = decltype(Ic)::value + 1;
+            v[16 + i] = cmul(v[16 + i], cmul(w16, w[i]));
+        });
+        const float2 w24 = cmul(w16, w8);
+        v[24] = cmul(v[24], w24);
+        static_for<7>([&](auto Ic) {
+            constexpr int i = decltype(Ic)::value + 1;
+            v[24 + i] = cmul(v[24 + i], cmul(w24, w[i]));
+        });
+    }
 }
 
 // ---------------------------------------------------------------- the fused work unit
@@ -360,14 +444,15 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
     if constexpr (P0 != P0_SIMT) {
         if (setup) tc_setup_afrags<P0>(afrag);
     }
-    // twiddle tables of the small passes: float4 [p][jm] = (w^{2p+1}, w^{2p+2}),
-    // w^k = exp(-2 pi i jm k / (Ns R))
+    // twiddle tables of the small passes, w^k = exp(-2 pi i jm k / (Ns R)): float4 [p][jm] =
+    // (w^{2p+1}, w^{2p+2}) for radix <= 8; for radix 16 and 32 the three pairs (w, w^2),
+    // (w^3, w^4), (w^8, w^16)
     for (int i = setup ? tid : S::TAB1 + S::TAB2; i < S::TAB1 + S::TAB2; i += kThreads) {
         int pass = i < S::TAB1 ? 1 : 2;
         int e = pass == 1 ? i : i - S::TAB1;
         int ns = S::ns(pass), R = S::radix(pass);
         int e4 = e >> 1, pr = e4 / ns, jm = e4 - pr * ns;
-        int k = 2 * pr + 1 + (e & 1);
+        int k = R >= 16 ? (pr < 2 ? 2 * pr + 1 + (e & 1) : 8 << (e & 1)) : 2 * pr + 1 + (e & 1);
         double sn = 0.0, cs = 0.0;
         if (k < R) sincospi(-2.0 * (double)(jm * k) / (double)(ns * R), &sn, &cs);
         tab[i] = make_float2((float)cs, (float)sn);
@@ -451,7 +536,8 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
                 const int j = t + T * b;
                 float2* u = v + b * R;
                 load_strided<N / R, R, S::PADP>(u, xch, j);
-                if constexpr (S::tab(1)) twiddle_tab<R, NS>(u, tab, j % NS);
+                if constexpr (S::tab(1) && R >= 16) twiddle_tab3<R, NS>(u, tab, j % NS);
+                else if constexpr (S::tab(1)) twiddle_tab<R, NS>(u, tab, j % NS);
                 else twiddle<R>(u, twb[b * T + t]);
                 dft<R>(u);
             });
@@ -476,7 +562,8 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
                 const int j = t + T * b;
                 float2* u = v + b * R;
                 load_strided<N / R, R, S::PADP>(u, xch, j);
-                if constexpr (S::tab(PL)) twiddle_tab<R, S::ns(PL)>(u, tab + TAB0, j % S::ns(PL));
+                if constexpr (S::tab(PL) && R >= 16) twiddle_tab3<R, S::ns(PL)>(u, tab + TAB0, j % S::ns(PL));
+                else if constexpr (S::tab(PL)) twiddle_tab<R, S::ns(PL)>(u, tab + TAB0, j % S::ns(PL));
                 else twiddle<R>(u, twb[(SLOT0 + b) * T + t]);
                 dft<R>(u);
                 static_for<R>([&](auto Qc) {
@@ -529,7 +616,7 @@ struct SchedWL {
     static constexpr int STAGE_WORDS = Sched<LOG2N>::STAGE_WORDS;
     static constexpr int OFF_MBAR = 0;
     static constexpr int OFF_TWB = 64;                        // [b][t] bases W_N^n (per CTA)
-    static constexpr int OFF_TABC = OFF_TWB + 8 * 1024;       // float4 [p][l] (W^{(2p+1) l}, W^{(2p+2) l})
+    static constexpr int OFF_TABC = OFF_TWB + 8 * 1024;       // float4 [3][l]: (w, w^2), (w^3, w^4), (w^8, w^16)
     static constexpr int OFF_STAGE = OFF_TABC + 8 * 32 * 32;
     static constexpr int OFF_REG = OFF_STAGE + 4 * STAGE_WORDS * G;
     static constexpr int SMEM = OFF_REG + 8 * RPAD * M * G;
@@ -576,10 +663,12 @@ __device__ __forceinline__ bool integrate_unit_wl(const KArgs a, const int gx, c
         sincospi(-2.0 * (double)n / (double)N, &sn, &cs);
         twb[i] = make_float2((float)cs, (float)sn);
     }
-    for (int i = setup ? tid : 32 * 32; i < 32 * 32; i += kThreads) {
-        const int e4 = i >> 1, pr = e4 / 32, l = e4 % 32, k = 2 * pr + 1 + (i & 1);
-        double sn = 0.0, cs = 0.0;
-        if (k < 32) sincospi(-2.0 * (double)(l * k) / 1024.0, &sn, &cs);
+    // three pairs per lane (w, w^2), (w^3, w^4), (w^8, w^16), w = W_1024^l (see twiddle_tab3)
+    for (int i = setup ? tid : 6 * 32; i < 6 * 32; i += kThreads) {
+        const int e4 = i >> 1, pr = e4 / 32, l = e4 % 32;
+        const int k = pr < 2 ? 2 * pr + 1 + (i & 1) : 8 << (i & 1);
+        double sn, cs;
+        sincospi(-2.0 * (double)(l * k) / 1024.0, &sn, &cs);
         tabc[i] = make_float2((float)cs, (float)sn);
     }
     __syncthreads();
@@ -679,7 +768,7 @@ __device__ __forceinline__ bool integrate_unit_wl(const KArgs a, const int gx, c
             constexpr int k = decltype(Kc)::value;
             v[k] = rw[lane + 34 * k];
         });
-        twiddle_tab<32, 32>(v, tabc, lane);
+        twiddle_tab3<32, 32>(v, tabc, lane);
         dft<32>(v);
         static_for<32>([&](auto Qc) {
             constexpr int q = decltype(Qc)::value;
