@@ -381,9 +381,9 @@ def _recorded_traffic(nfft, n_ranges, n_ipp, order):
             h.update(fh.read())
     if rec.get("kernel_source_sha256") != h.hexdigest():
         return None
-    if rec.get("workload") != {"n_ranges": n_ranges, "n_ipp": n_ipp} or rec.get("radix_order") != order:
+    if rec.get("workload") != {"n_ranges": n_ranges, "n_ipp": n_ipp}:
         return None
-    return rec.get("bytes_per_launch", {}).get(str(nfft))
+    return rec.get("bytes_per_launch", {}).get(str(nfft), {}).get(str(order))
 
 
 def main():
