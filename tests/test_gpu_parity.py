@@ -160,9 +160,12 @@ def test_ranges_override():
     assert_parity(out.numpy().astype(np.float64), ref, what="ranges override")
 
 
-def test_timeout_is_reported_and_context_survives():
+# 1024: a gate per warp (warp votes); 4096: four gates per CTA on their own named barriers;
+# 16384: one gate per CTA (CTA barrier)
+@pytest.mark.parametrize("nfft", [1024, 4096, 16384])
+def test_timeout_is_reported_and_context_survives(nfft):
     rng = np.random.default_rng(13)
-    nfft, R, P = 1024, 4, 5
+    R, P = 4, 5
     echo, tx = _rand_case(rng, nfft, R, P, start=0, step=25, L=nfft, kind="pm1", per=False)
     dev = torch.device("cuda:0")
     e = torch.from_numpy(echo).to(dev)
@@ -188,3 +191,18 @@ def test_device_generator_matches_host_generator():
     out = torch.empty((w.n_ipp, w.echo_stride, 2), dtype=torch.int16, device=dev)
     w.echo_device(out.data_ptr(), code_d.data_ptr())
     assert np.array_equal(out.cpu().numpy(), w.echo_host())
+
+
+def test_allocation_failure_is_reported_and_context_survives():
+    # 2^30 gates x 16384 bins of FP64 accumulators (128 TiB) cannot be allocated: the plan
+    # reports ISR_ERR_NO_MEMORY and the device stays usable
+    nfft, R = 16384, 1 << 30
+    with pytest.raises(isr.IsrError) as ei:
+        isr.Plan(nfft=nfft, n_ranges=R, echo_stride=R + nfft, range_step=1, device=0,
+                 stream=torch.cuda.current_stream())
+    assert ei.value.status == isr.ISR_ERR_NO_MEMORY
+    rng = np.random.default_rng(14)
+    echo, tx = _rand_case(rng, 1024, 4, 3, start=0, step=25, L=1024, kind="pm1", per=False)
+    got, _ = gpu_integrate(echo, tx, nfft=1024, n_ranges=4, range_step=25)
+    ref = oracle.integrate(echo, tx, nfft=1024, n_ranges=4, range_step=25)
+    assert_parity(got, ref, what="after allocation failure")
