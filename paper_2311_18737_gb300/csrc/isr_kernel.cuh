@@ -75,6 +75,10 @@ struct Sched {
     // shared-memory exchange buffer: one pad element per PADP keeps every access pattern
     // of the passes free of bank conflicts (stride R0 + 1 for the first pass' writes)
     static constexpr int PADP = R0 < 16 ? 16 : R0;
+    // the middle pass writes its outputs back into the slots it read (in place, no barrier
+    // between its reads and writes); the last pass then reads through the index permutation.
+    // Needs Ns = R0 = PADP for conflict-free, constant-offset permuted reads.
+    static constexpr bool INPLACE = NP == 3 && R0 >= 16;
     static constexpr int NPAD = NP > 1 ? N + N / PADP : 0;
     // window + alignment slack (16-byte multiple); at nfft 16384 room for the padded
     // 16-row layout of the tensor-core first pass
@@ -528,8 +532,26 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
         }
         if constexpr (NP == 1) continue;
 
-        // ---- middle pass (three-pass sizes): read all, barrier, write all
-        if constexpr (NP == 3) {
+        // ---- middle pass (three-pass sizes), in place: butterfly j reads x[j + (N/R) k] and
+        // writes its output X_j[q] to the same slots, j + (N/R) q, so no other thread touches
+        // them and no barrier separates the reads from the writes.  (Stockham element
+        // D = (j / Ns) Ns R + j % Ns + q Ns is X_j[q]; the last pass finds it there.)
+        if constexpr (S::INPLACE) {
+            constexpr int R = S::R1, NS = R0;
+            static_for<E / R>([&](auto Bc) {
+                constexpr int b = decltype(Bc)::value;
+                const int j = t + T * b;
+                float2* u = v + b * R;
+                load_strided<N / R, R, S::PADP>(u, xch, j);
+                if constexpr (S::tab(1) && R >= 16) twiddle_tab3<R, NS>(u, tab, j % NS);
+                else if constexpr (S::tab(1)) twiddle_tab<R, NS>(u, tab, j % NS);
+                else twiddle<R>(u, twb[b * T + t]);
+                dft<R>(u);
+                store_strided<N / R, R, S::PADP>(xch, j, u);
+            });
+            gsync();
+        } else if constexpr (NP == 3) {
+            // read all, barrier, write all (Stockham order)
             constexpr int R = S::R1, NS = R0;
             static_for<E / R>([&](auto Bc) {
                 constexpr int b = decltype(Bc)::value;
@@ -561,7 +583,13 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
                 constexpr int b = decltype(Bc)::value;
                 const int j = t + T * b;
                 float2* u = v + b * R;
-                load_strided<N / R, R, S::PADP>(u, xch, j);
+                if constexpr (S::INPLACE) {
+                    // Stockham element D = j + (N/R) k sits at k Ns1 + j % Ns1 + (N/R1) (j / Ns1)
+                    constexpr int NS1 = R0;
+                    load_strided<NS1, R, S::PADP>(u, xch, (j % NS1) + (N / S::R1) * (j / NS1));
+                } else {
+                    load_strided<N / R, R, S::PADP>(u, xch, j);
+                }
                 if constexpr (S::tab(PL) && R >= 16) twiddle_tab3<R, S::ns(PL)>(u, tab + TAB0, j % S::ns(PL));
                 else if constexpr (S::tab(PL)) twiddle_tab<R, S::ns(PL)>(u, tab + TAB0, j % S::ns(PL));
                 else twiddle<R>(u, twb[(SLOT0 + b) * T + t]);
