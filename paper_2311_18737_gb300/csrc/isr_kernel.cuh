@@ -6,9 +6,11 @@
 //      asynchronous copy (cp.async.bulk + mbarrier) that was issued one IPP ahead;
 //   2. decodes x[k] = conj(eps[k]) * m[s_r + k] on the fly while loading the first
 //      radix pass (Eq. 7 of the paper, the "complex multiplication" kernel of Sec. 3.2.1);
-//   3. runs a Stockham radix-32/16/8 FFT: each thread owns 32 points, every pass is a
-//      register-resident radix-R DFT, passes exchange data through a padded (bank-
-//      conflict-free) shared-memory buffer (the transform of Sec. 3.2.2);
+//   3. runs a three-pass Stockham FFT (radices 8..32 in one of several orders): each thread
+//      owns 32 points, every pass is a register-resident radix-R DFT, passes exchange data
+//      through a padded (bank-conflict-free) shared-memory buffer, and the middle pass works
+//      in place so that only three barriers of the gate separate the passes of an IPP (the
+//      transform of Sec. 3.2.2);
 //   4. adds |X[f]|^2 into 32 FP32 accumulators per thread that stay in registers for the
 //      whole IPP chunk (Eq. 8, the "spectrum accumulation" kernel of Sec. 3.2.3).
 // At the end of the chunk each thread writes its 32 partial sums once; a separate
@@ -28,7 +30,7 @@ constexpr int kThreads = 512;
 
 // ---------------------------------------------------------------- per-size schedule
 // Radix orders of the three-pass sizes (nfft 2048 .. 16384).  ORDER 0 is the default;
-// the batched launch may pick another per size (autotuned).
+// Plan.autotune and the batched launch time them on the caller's data and pick per size.
 __host__ __device__ constexpr int radix_of(int log2n, int order, int p)
 {
     if (log2n <= 5) return p == 0 ? (1 << log2n) : 1;
