@@ -128,11 +128,47 @@ __device__ __forceinline__ void dif_stage(float2* v)
     if constexpr (LEN > 2) dif_stage<R, LEN / 2>(v);
 }
 
-// In-place R-point forward DFT of v[0..R): afterwards V[q] = v[bitrev(q)].
-template <int R>
+// Two DIF radix-2 stages of sub-length LEN and LEN/2 fused (radix 2^2), then the rest.  With
+// a[i] = x[i] + x[i+L/2] and d[i] = x[i] - x[i+L/2] (L = LEN, i < L/4) the four quarters are
+//   a[i] + a[i+L/4],                (a[i] - a[i+L/4]) W_L^{2i},
+//   (d[i] - i d[i+L/4]) W_L^{i},    (d[i] + i d[i+L/4]) W_L^{3i},
+// the same values in the same places as two radix-2 stages (the output stays in bit-reversed
+// order), with the first stage's twiddles merged into the second: 3 (L/4 - 1) twiddle products
+// per block instead of L - 3.
+template <int R, int LEN>
+__device__ __forceinline__ void dif22_stage(float2* v)
+{
+    if constexpr (LEN == 2) {
+        dif_stage<R, 2>(v);
+    } else {
+        constexpr int Q = LEN / 4;
+        static_for<R / LEN>([&](auto Sb) {
+            constexpr int s = decltype(Sb)::value * LEN;
+            static_for<Q>([&](auto Iv) {
+                constexpr int i = decltype(Iv)::value;
+                const float2 x0 = v[s + i], x1 = v[s + i + Q], x2 = v[s + i + 2 * Q], x3 = v[s + i + 3 * Q];
+                const float2 a0 = cadd(x0, x2), a1 = cadd(x1, x3);
+                const float2 d0 = csub(x0, x2), d1 = csub(x1, x3);
+                v[s + i] = cadd(a0, a1);
+                v[s + i + Q] = mul_w<2 * i, LEN>(csub(a0, a1));
+                // d0 - i d1 = (d0.x + d1.y, d0.y - d1.x); d0 + i d1 = (d0.x - d1.y, d0.y + d1.x)
+                v[s + i + 2 * Q] = mul_w<i, LEN>(make_float2(d0.x + d1.y, d0.y - d1.x));
+                v[s + i + 3 * Q] = mul_w<3 * i, LEN>(make_float2(d0.x - d1.y, d0.y + d1.x));
+            });
+        });
+        if constexpr (LEN > 4) dif22_stage<R, LEN / 4>(v);
+    }
+}
+
+// In-place R-point forward DFT of v[0..R): afterwards V[q] = v[bitrev(q)].  R22 selects the
+// radix-2^2 network (fewer twiddle products, four values live per butterfly group).
+template <int R, bool R22 = false>
 __device__ __forceinline__ void dft(float2* v)
 {
-    if constexpr (R > 1) dif_stage<R, R>(v);
+    if constexpr (R > 1) {
+        if constexpr (R22) dif22_stage<R, R>(v);
+        else dif_stage<R, R>(v);
+    }
 }
 
 template <int R>
