@@ -513,7 +513,7 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
                 if (FULL || pos < a.code_len)
                     u[k] = decode<TXT>(stage[off + pos], txrow, pos, (signs << (31 - (b * R0 + k))) & 0x80000000u);
             });
-            dft<R0, LOG2N == 14>(u);
+            dft<R0, LOG2N >= 10>(u);
             if constexpr (NP == 1) {
                 static_for<R0>([&](auto Qc) {
                     constexpr int q = decltype(Qc)::value;
@@ -548,7 +548,7 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
                 if constexpr (S::tab(1) && R >= 16) twiddle_tab3<R, NS>(u, tab, j % NS);
                 else if constexpr (S::tab(1)) twiddle_tab<R, NS>(u, tab, j % NS);
                 else twiddle<R>(u, twb[b * T + t]);
-                dft<R, LOG2N == 14>(u);
+                dft<R, LOG2N >= 10>(u);
                 store_strided<N / R, R, S::PADP>(xch, j, u);
             });
             gsync();
@@ -563,7 +563,7 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
                 if constexpr (S::tab(1) && R >= 16) twiddle_tab3<R, NS>(u, tab, j % NS);
                 else if constexpr (S::tab(1)) twiddle_tab<R, NS>(u, tab, j % NS);
                 else twiddle<R>(u, twb[b * T + t]);
-                dft<R, LOG2N == 14>(u);
+                dft<R, LOG2N >= 10>(u);
             });
             gsync();
             static_for<E / R>([&](auto Bc) {
@@ -595,7 +595,7 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
                 if constexpr (S::tab(PL) && R >= 16) twiddle_tab3<R, S::ns(PL)>(u, tab + TAB0, j % S::ns(PL));
                 else if constexpr (S::tab(PL)) twiddle_tab<R, S::ns(PL)>(u, tab + TAB0, j % S::ns(PL));
                 else twiddle<R>(u, twb[(SLOT0 + b) * T + t]);
-                dft<R, LOG2N == 14>(u);
+                dft<R, LOG2N >= 10>(u);
                 static_for<R>([&](auto Qc) {
                     constexpr int q = decltype(Qc)::value;
                     float2 X = u[BitRev<R>::at(q)];
