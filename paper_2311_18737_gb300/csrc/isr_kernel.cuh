@@ -756,7 +756,7 @@ __device__ __forceinline__ bool integrate_unit_wl(const KArgs a, const int gx, c
                 if (FULL || pos < a.code_len)
                     u[k] = decode<TXT>(stage[off + pos], txrow, pos, (signs << (31 - (b * M + k))) & 0x80000000u);
             });
-            dft<M>(u);
+            dft<M, true>(u);
             const float2 w = twb[b * T + t];
             float2 cur = w;
             static_for<M>([&](auto Qc) {
@@ -785,7 +785,7 @@ __device__ __forceinline__ bool integrate_unit_wl(const KArgs a, const int gx, c
             constexpr int k = decltype(Kc)::value;
             v[k] = rw[lane + 34 * k];
         });
-        dft<32>(v);
+        dft<32, true>(v);
         __syncwarp();
         static_for<16>([&](auto Qc) {                       // y[32 l + q], q pairs: rw[34 l + q]
             constexpr int q = 2 * decltype(Qc)::value;
@@ -799,7 +799,7 @@ __device__ __forceinline__ bool integrate_unit_wl(const KArgs a, const int gx, c
             v[k] = rw[lane + 34 * k];
         });
         twiddle_tab3<32, 32>(v, tabc, lane);
-        dft<32>(v);
+        dft<32, true>(v);
         static_for<32>([&](auto Qc) {
             constexpr int q = decltype(Qc)::value;
             const float2 X = v[BitRev<32>::at(q)];
