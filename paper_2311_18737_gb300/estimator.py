@@ -12,7 +12,8 @@ nfft 16384, gate step 25, 50 MS/s, binary-phase code), a random Chapman layer (p
 150-850, scale height 60-160 gates, peak plasma-line frequency 3-15 MHz; line frequency
 proportional to sqrt(n_e)), per-gate SNR uniform in -30..0 dB, 15 % of gates without a
 line (and every gate whose line falls below 1.1 MHz), and 256 IPPs per integration.
-Spectra are ``ISR_MEAN`` averages; the network reads the 1-15 MHz band (bins 320-4927).
+Spectra are ``ISR_MEAN`` averages; the network reads the 1-15 MHz band (bins 320-4927), or with
+``--net-band full`` all 16384 bins; the peak fit always searches the 1-15 MHz band.
 
     python -m paper_2311_18737_gb300.estimator --train-integrations 200 --steps 3000 --out results.json
 """
@@ -154,11 +155,14 @@ def make_dataset(n_integrations: int, seed: int, n_ipp: int = 256, device: int =
             plan.spectra(spectra, isr.ISR_MEAN | isr.ISR_RESET_AFTER)
             feats.append(est.features(spectra))
             isr.isr_peak_fit(spectra, N_GATES, NFFT, BAND_LO, BAND_LO + BAND_LEN, fb, sr, stream)
-            pf_bin.append(fb.cpu().numpy() - BAND_LO)
+            # positions in the network's band coordinates; presence means a line inside the
+            # 1-15 MHz band whatever the network reads
+            pf_bin.append(fb.cpu().numpy() - est.band_lo)
             pf_snr.append(sr.cpu().numpy().astype(np.float64))
-            lb = f * NFFT - BAND_LO
+            lb = f * NFFT - est.band_lo
+            lp = f * NFFT - BAND_LO
             labels.append(lb)
-            pres.append(present & (lb >= 4) & (lb <= BAND_LEN - 5))
+            pres.append(present & (lp >= 4) & (lp <= BAND_LEN - 5))
             snrs.append(snr)
     if own:
         est.close()
@@ -200,7 +204,7 @@ def presence_threshold(data) -> float:
 
 def evaluate(est: Estimator, data, pf_threshold: float):
     pos, pres = est.predict(data["x"])
-    pos = pos.cpu().numpy().astype(np.float64) - BAND_LO
+    pos = pos.cpu().numpy().astype(np.float64) - est.band_lo
     pres = pres.cpu().numpy().astype(np.float64)
     y, truth, snr = data["present_np"], data["line_bin_np"].astype(np.float64), data["snr_db"]
     out = {"n_gates": int(y.size), "n_present": int(y.sum()),
@@ -235,9 +239,12 @@ def main():
     ap.add_argument("--precision", choices=["bf16", "fp32"], default="bf16")
     ap.add_argument("--out", default=None)
     ap.add_argument("--save-params", default=None)
+    ap.add_argument("--net-band", choices=["band", "full"], default="band",
+                    help="network input: the 1-15 MHz band or all nfft bins")
     a = ap.parse_args()
     prec = isr.ISR_EST_BF16 if a.precision == "bf16" else isr.ISR_EST_FP32
-    est = Estimator(max_batch=a.batch, precision=prec)
+    lo, ln = (BAND_LO, BAND_LEN) if a.net_band == "band" else (0, NFFT)
+    est = Estimator(max_batch=a.batch, precision=prec, band_lo=lo, band_len=ln)
     est.set_params(init_params(0))
     t0 = time.time()
     tr = make_dataset(a.train_integrations, seed=1, n_ipp=a.n_ipp, est=est)
@@ -250,7 +257,8 @@ def main():
     t_train = time.time() - t0
     res = evaluate(est, te, presence_threshold(tr))
     res.update({"train_spectra": int(tr["x"].shape[0]), "eval_spectra": int(te["x"].shape[0]), "n_ipp": a.n_ipp,
-                "steps": a.steps, "batch": a.batch, "precision": a.precision, "data_seconds": t_data,
+                "steps": a.steps, "batch": a.batch, "precision": a.precision, "net_band": [lo, lo + ln],
+                "data_seconds": t_data,
                 "train_seconds": t_train, "loss_history": hist})
     print(json.dumps(res, indent=1))
     if a.out:
