@@ -140,9 +140,9 @@ def _dist():
     return world, rank, local
 
 
-def max_over_ranks(values, device, world):
-    """Element-wise maximum of per-rank timings (no-op for one rank)."""
-    if world <= 1:
+def max_over_ranks(values, device, world, use_dist=None):
+    """Element-wise maximum of per-rank timings (no-op without a process group)."""
+    if not (world > 1 if use_dist is None else use_dist):
         return [float(v) for v in values]
     import torch
     import torch.distributed as dist
@@ -227,7 +227,10 @@ def run_ours(args):
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
+    # the multi-rank path (NCCL barriers and max over ranks) runs whenever torchrun launched the
+    # process, one rank included
+    use_dist = world > 1 or "TORCHELASTIC_RUN_ID" in os.environ
+    if use_dist:
         dist.init_process_group("nccl", device_id=dev)
 
     w = _workload(args.workload, rank, args.n_ranges, args.n_ipp)
@@ -262,7 +265,7 @@ def run_ours(args):
     sampler.start()
     time.sleep(0.3)
     info0 = plan.info()
-    if world > 1:
+    if use_dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -271,7 +274,7 @@ def run_ours(args):
         step(echo, code_d, out)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
-    if world > 1:
+    if use_dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     info1 = plan.info()
@@ -293,19 +296,19 @@ def run_ours(args):
         out_h = torch.empty((R, N), dtype=torch.float32, pin_memory=True)
         step(echo_h, code_h, out_h)
         torch.cuda.synchronize(dev)
-        if world > 1:
+        if use_dist:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             step(echo_h, code_h, out_h)
         e2e_ms = 1000 * (time.perf_counter() - t0) / args.e2e_steps
-        e2e_ms = max_over_ranks([e2e_ms], dev, world)[0]
+        e2e_ms = max_over_ranks([e2e_ms], dev, world, use_dist)[0]
         e2e = {"value": job_throughput(world, R, P, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(echo_h.numel() * 2 + code_h.numel()),
                "d2h_bytes_per_step": int(out_h.numel() * 4), "ms_per_step": e2e_ms}
         del echo_h
 
-    ms, kernel_ms = max_over_ranks([ms, kernel_ms], dev, world)
+    ms, kernel_ms = max_over_ranks([ms, kernel_ms], dev, world, use_dist)
 
     peaks = _peaks()
     props = torch.cuda.get_device_properties(dev)
@@ -358,7 +361,7 @@ def run_ours(args):
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
+    if use_dist:
         dist.barrier()
         dist.destroy_process_group()
     return 0

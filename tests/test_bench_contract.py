@@ -55,3 +55,23 @@ def test_our_arm_line():
     assert d["gpu_launches"] >= 2 * d["steps"]
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+
+
+@pytest.mark.gpu
+def test_torchrun_launch_one_rank():
+    # the launch the harness uses for N GPUs, here with one rank: NCCL process group, barriers
+    # and the max over ranks all run
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "1",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--gpus", "1", "--steps", "2", "--warmup", "3", "--n-ranges", "32", "--n-ipp", "64",
+                        "--e2e-steps", "1", "--no-cpu-baseline", "--no-peak"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 1 and d["value"] > 0 and d["e2e"]["value"] > 0
