@@ -63,7 +63,8 @@ struct DeviceGuard {
 constexpr unsigned kDefaultWaitLimit = 1u << 22;
 constexpr int kDefaultChunk = 256;
 constexpr int64_t kScratchBudget = int64_t(4) << 30;   // bytes of chunk partials
-constexpr int64_t kHostStageBytes = int64_t(512) << 20; // per host-input staging buffer
+constexpr int64_t kHostStageBytes = int64_t(1) << 30;   // per host-input staging buffer
+constexpr int64_t kHostFirstBytes = int64_t(64) << 20;   // first block of a host-input call
 
 int chip_bytes(int tx_type) { return tx_type == ISR_TX_CI16 ? 4 : tx_type == ISR_TX_C32 ? 8 : 1; }
 
@@ -285,10 +286,13 @@ isr_status integrate_host(isr_plan* p, const int16_t* echo, const void* tx, int6
     const int cb = chip_bytes(p->d.tx_type);
     const char* txc = static_cast<const char*>(tx);
     bool tx_dev = is_device_ptr(tx);
+    // a small first block gets the kernels going after a short copy; then blocks as large as a
+    // staging buffer, so a call makes few launches (each launch ends with a partly filled wave)
+    const int64_t first = std::max<int64_t>(1, std::min<int64_t>(rows, kHostFirstBytes / row_bytes));
     int blk = 0;
-    for (int64_t done = 0; done < n; done += rows, ++blk) {
+    for (int64_t done = 0, nb = 0; done < n; done += nb, ++blk) {
         const int b = blk & 1;
-        const int64_t nb = std::min(rows, n - done);
+        nb = std::min(blk == 0 ? first : rows, n - done);
         CUDA_TRY(cudaStreamWaitEvent(p->copy_stream, p->hs_free[b], 0));
         CUDA_TRY(cudaMemcpyAsync(p->hs_echo[b], echo + done * p->d.echo_stride * 2, (size_t)(nb * row_bytes),
                                  cudaMemcpyHostToDevice, p->copy_stream));
