@@ -286,9 +286,10 @@ isr_status integrate_host(isr_plan* p, const int16_t* echo, const void* tx, int6
     const int cb = chip_bytes(p->d.tx_type);
     const char* txc = static_cast<const char*>(tx);
     bool tx_dev = is_device_ptr(tx);
-    // a small first block gets the kernels going after a short copy; then blocks as large as a
-    // staging buffer, so a call makes few launches (each launch ends with a partly filled wave)
-    const int64_t first = std::max<int64_t>(1, std::min<int64_t>(rows, kHostFirstBytes / row_bytes));
+    // a call larger than one staging buffer starts with a small block, so the kernels get going
+    // after a short copy, then goes on in blocks as large as a buffer (few launches: each launch
+    // ends with a partly filled wave); a call that fits one buffer is one block
+    const int64_t first = n > rows ? std::max<int64_t>(1, std::min<int64_t>(rows, kHostFirstBytes / row_bytes)) : rows;
     int blk = 0;
     for (int64_t done = 0, nb = 0; done < n; done += nb, ++blk) {
         const int b = blk & 1;
