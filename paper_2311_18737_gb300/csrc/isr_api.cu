@@ -79,25 +79,37 @@ bool is_device_ptr(const void* p)
 }
 
 // sum of chunk partials into the FP64 accumulators: acc[i] += sum_c part[c][i]
+// s + x with the rounding error carried in c (Kahan compensated summation, FP32)
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// acc[i] += sum_c part[c][i]: the chunk partials are summed in FP32 with compensation (error
+// ~2 ulp whatever the chunk count) and added once per bin into the FP64 accumulator, so the
+// kernel streams at memory speed instead of waiting on FP64 conversions and additions
 __global__ void reduce_partials_kernel(const float* __restrict__ part, int n_chunks, int64_t n,
                                        double* __restrict__ acc)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i < n; i += stride) {
-        double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        float s[4] = {0.f, 0.f, 0.f, 0.f}, cp[4] = {0.f, 0.f, 0.f, 0.f};
         for (int c = 0; c < n_chunks; ++c) {
-            float4 v = __ldcs(reinterpret_cast<const float4*>(part + (int64_t)c * n + i));
-            s0 += v.x;
-            s1 += v.y;
-            s2 += v.z;
-            s3 += v.w;
+            const float4 v = __ldcs(reinterpret_cast<const float4*>(part + (int64_t)c * n + i));
+            kahan_add(s[0], cp[0], v.x);
+            kahan_add(s[1], cp[1], v.y);
+            kahan_add(s[2], cp[2], v.z);
+            kahan_add(s[3], cp[3], v.w);
         }
         double2* a = reinterpret_cast<double2*>(acc + i);
         double2 a0 = a[0], a1 = a[1];
-        a0.x += s0;
-        a0.y += s1;
-        a1.x += s2;
-        a1.y += s3;
+        a0.x += (double)s[0] - (double)cp[0];
+        a0.y += (double)s[1] - (double)cp[1];
+        a1.x += (double)s[2] - (double)cp[2];
+        a1.y += (double)s[3] - (double)cp[3];
         a[0] = a0;
         a[1] = a1;
     }

@@ -135,13 +135,19 @@ struct RedSeg {
 };
 
 // out[i] = (float) sum_c part[c][i] in double, one window per blockIdx.y
+// out[i] = sum_c part[c][i], FP32 with Kahan compensation (error ~2 ulp for any chunk count)
 __global__ void batch_reduce_kernel(const RedSeg* __restrict__ segs)
 {
     const RedSeg s = segs[blockIdx.y];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += (int64_t)gridDim.x * blockDim.x) {
-        double acc = 0;
-        for (int c = 0; c < s.chunks; ++c) acc += s.part[(int64_t)c * s.n + i];
-        s.out[i] = (float)acc;
+        float sum = 0.f, comp = 0.f;
+        for (int c = 0; c < s.chunks; ++c) {
+            const float y = s.part[(int64_t)c * s.n + i] - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+        s.out[i] = (float)((double)sum - (double)comp);
     }
 }
 
