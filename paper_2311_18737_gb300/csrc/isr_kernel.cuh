@@ -443,9 +443,9 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
         int b = pass == 1 ? slot : slot - S::SLOTS1;
         int ns = S::ns(pass), R = S::radix(pass);
         int j = tt + T * b;
-        double sn, cs;
-        sincospi(-2.0 * (double)(j % ns) / (double)(ns * R), &sn, &cs);
-        twb[i] = make_float2((float)cs, (float)sn);
+        float sn, cs;   // the argument is an exact dyadic fraction; FP32 keeps setup off the FP64 pipe
+        sincospif(-2.f * (float)(j % ns) / (float)(ns * R), &sn, &cs);
+        twb[i] = make_float2(cs, sn);
     }
     if constexpr (P0 != P0_SIMT) {
         if (setup) tc_setup_afrags<P0>(afrag);
@@ -459,9 +459,9 @@ __device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, cons
         int ns = S::ns(pass), R = S::radix(pass);
         int e4 = e >> 1, pr = e4 / ns, jm = e4 - pr * ns;
         int k = R >= 16 ? (pr < 2 ? 2 * pr + 1 + (e & 1) : 8 << (e & 1)) : 2 * pr + 1 + (e & 1);
-        double sn = 0.0, cs = 0.0;
-        if (k < R) sincospi(-2.0 * (double)(jm * k) / (double)(ns * R), &sn, &cs);
-        tab[i] = make_float2((float)cs, (float)sn);
+        float sn = 0.f, cs = 0.f;
+        if (k < R) sincospif(-2.f * (float)(jm * k) / (float)(ns * R), &sn, &cs);
+        tab[i] = make_float2(cs, sn);
     }
     __syncthreads();
 
@@ -689,17 +689,17 @@ __device__ __forceinline__ bool integrate_unit_wl(const KArgs a, const int gx, c
     for (int i = setup ? tid : 1024; i < 1024; i += kThreads) {   // bases W_N^n, slot [b][t]
         const int b = i / T, tt = i - b * T;
         const int n = 2 * (tt + T * (b >> 1)) + (b & 1);
-        double sn, cs;
-        sincospi(-2.0 * (double)n / (double)N, &sn, &cs);
-        twb[i] = make_float2((float)cs, (float)sn);
+        float sn, cs;
+        sincospif(-2.f * (float)n / (float)N, &sn, &cs);
+        twb[i] = make_float2(cs, sn);
     }
     // three pairs per lane (w, w^2), (w^3, w^4), (w^8, w^16), w = W_1024^l (see twiddle_tab3)
     for (int i = setup ? tid : 6 * 32; i < 6 * 32; i += kThreads) {
         const int e4 = i >> 1, pr = e4 / 32, l = e4 % 32;
         const int k = pr < 2 ? 2 * pr + 1 + (i & 1) : 8 << (i & 1);
-        double sn, cs;
-        sincospi(-2.0 * (double)(l * k) / 1024.0, &sn, &cs);
-        tabc[i] = make_float2((float)cs, (float)sn);
+        float sn, cs;
+        sincospif(-2.f * (float)(l * k) / 1024.f, &sn, &cs);
+        tabc[i] = make_float2(cs, sn);
     }
     __syncthreads();
     if (t == 0 && p_begin < p_end && p_begin != a.drop_ipp) issue(p_begin);
