@@ -60,11 +60,11 @@ __device__ __noinline__ bool run_unit(const BatchWin& w, const BatchUnit& u, uns
 {
     if constexpr (O == 3) {
         using S = isr::SchedWL<L>;
-        return isr::integrate_unit_wl<L, isr::TX_PM1, false>(w.a, u.gx, u.cy, smem, s_phase[threadIdx.x / S::T],
+        return isr::integrate_unit_wl<L, isr::TX_PM1, false, const isr::KArgs&>(w.a, u.gx, u.cy, smem, s_phase[threadIdx.x / S::T],
                                                              setup);
     } else {
         using S = isr::Sched<L, O>;
-        return isr::integrate_unit<L, isr::TX_PM1, O>(w.a, u.gx, u.cy, smem, s_phase[threadIdx.x / S::T], setup);
+        return isr::integrate_unit<L, isr::TX_PM1, O, false, isr::P0_SIMT, const isr::KArgs&>(w.a, u.gx, u.cy, smem, s_phase[threadIdx.x / S::T], setup);
     }
 }
 
@@ -76,6 +76,10 @@ __global__ void __launch_bounds__(isr::kThreads, 1) batch_kernel(const BatchWin*
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t s_phase[8];
     __shared__ int s_unit;
+    // the current unit and its window's arguments: read from shared memory where a unit needs
+    // them instead of being held in registers for the whole unit
+    __shared__ BatchUnit s_u;
+    __shared__ BatchWin s_w;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);   // slot g at byte 8 g for every shape
     if (threadIdx.x < 8) {
         isr::mbar_init(isr::smem_u32(&mbar[threadIdx.x]), 1);
@@ -85,12 +89,18 @@ __global__ void __launch_bounds__(isr::kThreads, 1) batch_kernel(const BatchWin*
     int prev_key = -1;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+        if (threadIdx.x == 0) {
+            const int ui = atomicAdd(counter, 1);
+            s_unit = ui;
+            if (ui < n_units) {
+                s_u = units[ui];
+                s_w = wins[s_u.win];
+            }
+        }
         __syncthreads();
-        const int ui = s_unit;
-        if (ui >= n_units) break;
-        const BatchUnit u = units[ui];
-        const BatchWin& w = wins[u.win];
+        if (s_unit >= n_units) break;
+        const BatchUnit& u = s_u;
+        const BatchWin& w = s_w;
         const int key = w.log2n * 4 + w.order;
         const bool setup = key != prev_key;
         bool ok = true;

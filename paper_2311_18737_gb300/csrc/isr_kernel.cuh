@@ -357,8 +357,10 @@ __device__ __forceinline__ void twiddle_tab3(float2* v, const float2* tab, int j
 // Returns false if a staged-window wait ran out.
 // P0 selects the engine of the first pass: the SIMT radix-R0 DFT, or (nfft 16384, radix
 // order 1, binary-phase, full-length codes only) a split-precision tensor-core GEMM.
-template <int LOG2N, int TXT, int ORDER = 0, bool FULL = false, int P0 = P0_SIMT>
-__device__ __forceinline__ bool integrate_unit(const KArgs a, const int gx, const int c, unsigned char* smem,
+// A is how the arguments arrive: by value from a kernel parameter, or (persistent kernels) as a
+// reference to a shared-memory copy, read where needed rather than held in registers.
+template <int LOG2N, int TXT, int ORDER = 0, bool FULL = false, int P0 = P0_SIMT, class A = const KArgs>
+__device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, unsigned char* smem,
                                                const uint32_t phase0, const bool setup)
 {
     using S = Sched<LOG2N, ORDER>;
@@ -656,8 +658,8 @@ struct SchedWL {
 // two pad elements per 32 keep even elements 16-byte aligned for paired stores
 __device__ __forceinline__ int pid32(int i) { return i + 2 * (i >> 5); }
 
-template <int LOG2N, int TXT, bool FULL>
-__device__ __forceinline__ bool integrate_unit_wl(const KArgs a, const int gx, const int c, unsigned char* smem,
+template <int LOG2N, int TXT, bool FULL, class A = const KArgs>
+__device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c, unsigned char* smem,
                                                   const uint32_t phase0, const bool setup)
 {
     using S = SchedWL<LOG2N>;
