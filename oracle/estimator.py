@@ -22,6 +22,11 @@ Loss per gate (averaged over the batch), with presence label y and line position
 from `lo`): BCE(q, y) + y * CE(softmax(z), t), t_i proportional to exp(-(i - f)^2 / 2).
 Prediction: presence sigmoid(q); position = softmax-weighted mean of i over the 7 bins
 around argmax z.
+
+Storage precision: the network's BF16 variant keeps the input, the conv weights W1..W4 and
+every activation h1..h4 in BF16 (8 significant bits) and computes in FP32.  `forward`,
+`loss_and_grad` and `predict` take an optional `store` function applied at exactly those
+points (`round_bf16` for that variant; None keeps every value in double precision).
 """
 from __future__ import annotations
 
@@ -63,6 +68,15 @@ def init_params(seed: int = 0):
     return pack(d)
 
 
+def round_bf16(a):
+    """Nearest BF16 value (8 significant bits, ties to even) of FP32-representable values,
+    as float64: keep the upper 16 bits of the FP32 encoding after adding half of the
+    dropped part, plus one where the kept part is odd (the tie rule)."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def features(P, lo: int, L: int):
     y = np.log(np.maximum(np.asarray(P, dtype=np.float64)[:, lo:lo + L], 1e-30))
     m = y.mean(axis=1, keepdims=True)
@@ -90,13 +104,15 @@ def target(f_true, L):
     return np.where(s > 0, t / np.where(s > 0, s, 1.0), 0.0)
 
 
-def forward(theta, x):
+def forward(theta, x, store=None):
     p = unpack(theta)
-    x = np.asarray(x, dtype=np.float64)
+    keep = store if store is not None else (lambda v: v)
+    x = keep(np.asarray(x, dtype=np.float64))
     cache = {"h0": x[:, None, :]}
     h = cache["h0"]
     for l in range(1, 5):
-        h = np.maximum(conv(h, p[f"W{l}"], p[f"b{l}"]), 0.0)
+        cache[f"W{l}"] = keep(p[f"W{l}"])
+        h = keep(np.maximum(conv(h, cache[f"W{l}"], p[f"b{l}"]), 0.0))
         cache[f"h{l}"] = h
     z = np.einsum("c,bcl->bl", p["w5"], h) + p["b5"][0]
     amax = h.argmax(axis=2)                      # first index of the maximum
@@ -122,9 +138,9 @@ def loss(theta, x, f_true, y):
     return float(np.mean(bce + np.where(y > 0, y * ce, 0.0)))
 
 
-def loss_and_grad(theta, x, f_true, y):
+def loss_and_grad(theta, x, f_true, y, store=None):
     p = unpack(theta)
-    z, q, cache = forward(theta, x)
+    z, q, cache = forward(theta, x, store)
     B, L = z.shape
     y = np.asarray(y, dtype=np.float64)
     pi = softmax(z)
@@ -164,7 +180,7 @@ def loss_and_grad(theta, x, f_true, y):
             dap = np.zeros((B, C, L + 2 * HALF))
             dap[:, :, HALF:HALF + L] = da
             dprev = np.zeros_like(hprev)
-            W = p[f"W{l}"]
+            W = cache[f"W{l}"]
             for k in range(K):
                 # h_prev[j] feeds a[i] with i = j - k + HALF
                 dprev += np.einsum("oc,bol->bcl", W[:, :, k], dap[:, :, 2 * HALF - k:2 * HALF - k + L])
@@ -172,8 +188,8 @@ def loss_and_grad(theta, x, f_true, y):
     return total, pack(g)
 
 
-def predict(theta, x):
-    z, q, _ = forward(theta, x)
+def predict(theta, x, store=None):
+    z, q, _ = forward(theta, x, store)
     pi = softmax(z)
     B, L = z.shape
     i0 = z.argmax(axis=1)

@@ -71,3 +71,45 @@ def test_prediction_of_sharp_logits():
     x[0, 20] = 1.0
     pos, pres = est.predict(theta, x)
     assert abs(pos[0] - 20.0) < 1e-9 and abs(pres[0] - 0.5) < 1e-12
+
+
+def test_round_bf16_definition():
+    """BF16 keeps 8 significant bits, ties to the even neighbour: hand-worked values, the
+    BF16 grid is left alone, and torch's own FP32 -> BF16 conversion agrees."""
+    import torch
+
+    u = 2.0 ** -7                                  # BF16 spacing in [1, 2)
+    cases = {1.0: 1.0, 1 + u / 2: 1.0, 1 + 3 * u / 2: 1 + 2 * u, 1 + u / 2 + 2.0 ** -20: 1 + u,
+             -(1 + 3 * u / 2): -(1 + 2 * u), 255.0: 255.0, 257.0: 256.0, 259.0: 260.0, 0.0: 0.0}
+    for v, r in cases.items():
+        assert est.round_bf16(np.array([v]))[0] == r, v
+    grid = np.array([1 + k * u for k in range(128)] + [-3.0, 0.5, 2.0 ** -20])
+    assert np.array_equal(est.round_bf16(grid), grid)
+    rng = np.random.default_rng(9)
+    v = (rng.standard_normal(10000) * 10.0 ** rng.uniform(-6, 6, 10000)).astype(np.float32)
+    want = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(est.round_bf16(v), want)
+
+
+def test_storage_rounding_is_applied_where_the_bf16_variant_stores():
+    """With store=round_bf16 the forward equals a plain forward whose conv weights and input
+    were rounded first, when no activation needs rounding (every value is then on the BF16
+    grid), and it differs from the plain forward when the input is off the grid."""
+    d = est.unpack(np.zeros(est.N_PARAMS))
+    for l in range(1, 5):
+        W = np.zeros_like(d[f"W{l}"])
+        W[0, 0, est.HALF] = 1.0 + 2.0 ** -10       # rounds to 1 in BF16
+        d[f"W{l}"] = W
+    d["w5"][0] = 1.0
+    theta = est.pack(d)
+    x = np.array([[0.0, 1.0, 2.0, -1.0, 3.0, 0.5] + [0.0] * 10])
+    z_st, _, c = est.forward(theta, x, est.round_bf16)
+    dr = {k: v.copy() for k, v in d.items()}
+    for l in range(1, 5):
+        dr[f"W{l}"] = est.round_bf16(d[f"W{l}"])
+    z_pre, _, _ = est.forward(est.pack(dr), x)
+    assert np.array_equal(z_st, z_pre)
+    assert np.array_equal(z_st[0, :6], np.maximum(x[0, :6], 0))
+    x_off = x + 2.0 ** -12                          # off the BF16 grid near 1, 2, 3
+    z_off, _, _ = est.forward(theta, x_off, est.round_bf16)
+    assert not np.array_equal(z_off, est.forward(theta, x_off)[0])
