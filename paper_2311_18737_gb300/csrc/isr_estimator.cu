@@ -99,9 +99,12 @@ __global__ void cast_kernel(const float* __restrict__ in, size_t n, T* __restric
 }
 
 // working conv weights: forward layout [ci][k][co] and the backward-data layout of the
-// flipped transpose, [co][k'][ci] = W[co][ci][8 - k'] (both in the storage type)
+// flipped transpose, [co][k'][ci] = W[co][ci][8 - k'] (both in the storage type); with
+// tf and tb (tensor-core path, layers 2-4) also the GEMM rows [co][k][ci] of the forward
+// weights and [ci][k'][co] of the flipped transpose
 template <class T>
-__global__ void relayout_kernel(const float* __restrict__ theta, T* __restrict__ wf, T* __restrict__ wb)
+__global__ void relayout_kernel(const float* __restrict__ theta, T* __restrict__ wf, T* __restrict__ wb,
+                                T* __restrict__ tf, T* __restrict__ tb)
 {
     // layers 1..4 packed back to back: layer 1 has Cin = 1
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -119,6 +122,10 @@ __global__ void relayout_kernel(const float* __restrict__ theta, T* __restrict__
     size_t base = l == 1 ? 0 : (size_t)n1 + (size_t)(l - 2) * n;
     wf[base + ((size_t)ci * KT + k) * CH + co] = cvt<T>(w);
     if (l > 1) wb[(size_t)(l - 2) * n + ((size_t)co * KT + (KT - 1 - k)) * CH + ci] = cvt<T>(w);
+    if (l > 1 && tf) {
+        tf[(size_t)(l - 2) * n + ((size_t)co * KT + k) * CH + ci] = cvt<T>(w);
+        tb[(size_t)(l - 2) * n + ((size_t)ci * KT + (KT - 1 - k)) * CH + co] = cvt<T>(w);
+    }
 }
 
 // ---------------------------------------------------------------- convolution
@@ -178,6 +185,274 @@ __global__ void __launch_bounds__(256) conv_kernel(const TIN* __restrict__ in, c
             ob[i] = cvt<TOUT>(v);
         }
     }
+}
+
+// ---------------------------------------------------------------- tensor-core convolution
+// Layers 2-4 (32 -> 32 channels) with BF16 storage, as a GEMM on the warp-level tensor-core
+// instruction mma.m16n8k16 (BF16 operands, FP32 accumulation):
+//   out[co][i] = sum_kk A[co][kk] B[kk][i],   kk = 32 k + ci,   B[kk][i] = in[ci][i + k - 4],
+// with A the weights in [co][k][ci] order (K = 288).  B is never formed: the CTA stages its
+// input as a position-major tile, one 80-byte row of 32 channels per position (halo included),
+// so the 8 x 8 blocks of B at tap k are rows i + k of that tile and ldmatrix reads them as they
+// are.  Row pitches of 80 B (tile) and 592 B (weights) put the eight rows an ldmatrix reads on
+// 32 distinct banks.  The backward-data convolution is the same GEMM on the flipped transposed
+// weights; its FP32 input (the gradient) is split into two BF16 parts, hi + lo, and both are
+// multiplied, so the products keep ~16 bits of the gradient and the FP32 accumulation.
+// CTA: 256 positions x 32 output channels; warp w: positions [32 w, 32 w + 32), all channels.
+constexpr int TC_CT = 256;                 // positions per CTA
+constexpr int TC_XW = TC_CT + KT - 1;      // staged positions, halo included
+constexpr int TC_XR = CH + 8;              // bf16 per staged position (80 B)
+constexpr int TC_K = KT * CH;              // GEMM depth
+constexpr int TC_WR = TC_K + 8;            // bf16 per staged weight row (592 B)
+constexpr int TC_OR = TC_CT + 8;           // output staging row (elements)
+constexpr size_t tc_smem_bytes(bool fwd)
+{
+    return (size_t)2 * ((fwd ? 1 : 2) * TC_XW * TC_XR + CH * TC_WR);
+}
+static_assert(TC_XW * (CH / 2) % 32 == 0, "input staging assigns whole warps");
+static_assert((size_t)CH * TC_OR * 4 <= (size_t)2 * 2 * TC_XW * TC_XR, "FP32 output tile fits the input tiles");
+static_assert((size_t)CH * TC_OR * 2 <= (size_t)2 * TC_XW * TC_XR, "BF16 output tile fits the input tile");
+
+// BF16 storage runs the 32 -> 32 channel convolutions on the tensor cores
+template <class T> constexpr bool kTensorConv = false;
+template <> constexpr bool kTensorConv<__nv_bfloat16> = true;
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+// FWD: in = BF16 activations [B][32][L], out = BF16 relu(conv + bias).
+// !FWD: in = FP32 gradient [B][32][L], out = FP32 conv masked by mask > 0 (BF16 activations
+// of the layer below), no bias.
+template <bool FWD>
+__global__ void __launch_bounds__(256) conv_tc_kernel(const void* __restrict__ in, const __nv_bfloat16* __restrict__ wt,
+                                                      const float* __restrict__ bias,
+                                                      const __nv_bfloat16* __restrict__ mask, int L,
+                                                      void* __restrict__ out)
+{
+    constexpr int NX = FWD ? 1 : 2;                    // staged input parts
+    constexpr int XWORDS = TC_XW * TC_XR / 2;          // 32-bit words per staged part
+    extern __shared__ __align__(16) unsigned char tc_smem[];
+    uint32_t* xs = reinterpret_cast<uint32_t*>(tc_smem);
+    uint4* ws = reinterpret_cast<uint4*>(tc_smem + (size_t)4 * NX * XWORDS);
+    const int b = blockIdx.y, i0 = blockIdx.x * TC_CT;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // weights: [co][288] rows, 16-byte copies into 592-byte rows
+    const uint4* w4 = reinterpret_cast<const uint4*>(wt);
+    for (int e = tid; e < CH * (TC_K / 8); e += 256) {
+        const int co = e / (TC_K / 8), q = e - co * (TC_K / 8);
+        ws[co * (TC_WR / 8) + q] = w4[e];
+    }
+    // input: word (j, cp) holds channels 2 cp and 2 cp + 1 at position i0 - 4 + j; a warp
+    // takes 8 positions x 4 channel pairs, so its stores hit 32 distinct banks
+    for (int w = tid; w < TC_XW * (CH / 2); w += 256) {
+        const int grp = w >> 5, l = w & 31;
+        const int j = (grp >> 2) * 8 + (l & 7), cp = (grp & 3) * 4 + (l >> 3);
+        const int pos = i0 - HALF + j;
+        const size_t o = ((size_t)b * CH + 2 * cp) * L + pos;
+        const bool inside = pos >= 0 && pos < L;
+        if constexpr (FWD) {
+            const unsigned short* src = reinterpret_cast<const unsigned short*>(in);
+            const uint32_t v0 = inside ? src[o] : 0u, v1 = inside ? src[o + L] : 0u;
+            xs[j * (TC_XR / 2) + cp] = v0 | (v1 << 16);
+        } else {
+            const float* src = static_cast<const float*>(in);
+            const float v0 = inside ? src[o] : 0.f, v1 = inside ? src[o + L] : 0.f;
+            uint32_t hi, lo;
+            isr::split2<true>(v0, v1, hi, lo);
+            xs[j * (TC_XR / 2) + cp] = hi;
+            xs[XWORDS + j * (TC_XR / 2) + cp] = lo;
+        }
+    }
+    __syncthreads();
+
+    float acc[2][4][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
+    const uint32_t xs_s = isr::smem_u32(xs), ws_s = isr::smem_u32(ws);
+    const int r8 = lane & 7, mq = lane >> 3;
+    // ldmatrix rows: weights, matrix mq = (rows +8 if mq odd, columns +8 if mq >= 2), giving
+    // the A fragment registers in order; tile, matrix mq = (n-tile mq / 2, channels +8 if mq
+    // odd), giving (b0, b1) of two n-tiles
+    const uint32_t a_row = ws_s + 2u * (uint32_t)(((mq & 1) * 8 + r8) * TC_WR + (mq >> 1) * 8);
+    const uint32_t b_row = xs_s + 2u * (uint32_t)((warp * 32 + (mq >> 1) * 8 + r8) * TC_XR + (mq & 1) * 8);
+#pragma unroll 2
+    for (int s = 0; s < TC_K / 16; ++s) {              // k-step s: tap s / 2, channels 16 (s % 2) ..
+        const int tap = s >> 1, ci0 = (s & 1) * 16;
+        uint32_t a[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) ldsm_x4(a[mt], a_row + 2u * (uint32_t)(mt * 16 * TC_WR + s * 16));
+#pragma unroll
+        for (int part = 0; part < NX; ++part) {
+            uint32_t bq[2][4];
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+                ldsm_x4(bq[p], b_row + 4u * (uint32_t)(part * XWORDS) + 2u * (uint32_t)((p * 16 + tap) * TC_XR + ci0));
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const uint4 af = make_uint4(a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+                    isr::mma16816<true>(acc[mt][nt], af, bq[nt >> 1][(nt & 1) * 2], bq[nt >> 1][(nt & 1) * 2 + 1]);
+            }
+        }
+    }
+    __syncthreads();   // every warp is done with the tiles: the output tile reuses them
+
+    // accumulator (mt, nt, q): channel mt 16 + g + 8 (q >= 2), position 32 warp + 8 nt + 2 t + (q & 1)
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int co = mt * 16 + h * 8 + g;
+            const float bv = FWD ? __ldg(bias + co) : 0.f;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int pl = warp * 32 + nt * 8 + 2 * t4;
+                const float v0 = acc[mt][nt][2 * h] + bv, v1 = acc[mt][nt][2 * h + 1] + bv;
+                if constexpr (FWD)
+                    reinterpret_cast<uint32_t*>(tc_smem)[(co * TC_OR + pl) / 2] =
+                        isr::pack2<true>(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+                else
+                    reinterpret_cast<float2*>(tc_smem)[(co * TC_OR + pl) / 2] = make_float2(v0, v1);
+            }
+        }
+    __syncthreads();
+    // coalesced rows: warp w writes channels w, w + 8, w + 16, w + 24
+    for (int co = warp; co < CH; co += 8) {
+        const size_t row = ((size_t)b * CH + co) * L;
+        for (int q = lane; q < TC_CT; q += 32) {
+            const int i = i0 + q;
+            if (i >= L) break;
+            if constexpr (FWD) {
+                static_cast<__nv_bfloat16*>(out)[row + i] = reinterpret_cast<const __nv_bfloat16*>(tc_smem)[co * TC_OR + q];
+            } else {
+                const float v = reinterpret_cast<const float*>(tc_smem)[co * TC_OR + q];
+                static_cast<float*>(out)[row + i] = __bfloat162float(mask[row + i]) > 0.f ? v : 0.f;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], uint32_t addr)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t (&r)[2], uint32_t addr)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(addr));
+}
+
+// Weight gradient of layers 2-4 with BF16 storage on the tensor cores:
+//   dW[co][ci][k] = sum_{b,i} da[b][co][i] h[b][ci][i + k - 4],  db[co] = sum_{b,i} da[b][co][i],
+// the GEMM D[co][kk] = sum_i A[co][i] B[i][kk] with kk = (k, ci), A = da (FP32, split into BF16
+// hi + lo, both multiplied) and B[i][(k, ci)] = h[ci][i + k - 4].  B's 8 x 8 blocks are read
+// transposed (ldmatrix.trans) from the position-major activation tile of the forward kernel,
+// whose rows i + k start on 16-byte boundaries for every tap k.  CTA: WT_SPAN positions of one
+// row in chunks of TC_CT; warp w: output channels 16 (w % 2) .., input channels 8 (w / 2) ..
+// at all 9 taps; the CTA's partial dW and db are added with one atomic per element.
+constexpr int WT_SPAN = 1024;
+constexpr int WT_DR = TC_CT + 8;   // bf16 per staged gradient row (528 B)
+constexpr size_t wgrad_tc_smem_bytes() { return (size_t)2 * (2 * CH * WT_DR + TC_XW * TC_XR); }
+
+__global__ void __launch_bounds__(256) wgrad_tc_kernel(const __nv_bfloat16* __restrict__ h, const float* __restrict__ da,
+                                                       int L, float* __restrict__ dW, float* __restrict__ db)
+{
+    extern __shared__ __align__(16) unsigned char wt_smem[];
+    uint32_t* dah = reinterpret_cast<uint32_t*>(wt_smem);   // [CH][WT_DR / 2] words, hi parts
+    uint32_t* dal = dah + CH * WT_DR / 2;                   // lo parts
+    uint32_t* xs = dal + CH * WT_DR / 2;                    // [TC_XW][TC_XR / 2] words
+    __shared__ float db_s[CH];
+    const int b = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < CH) db_s[tid] = 0.f;
+    const int mt = warp & 1, ci0 = (warp >> 1) * 8;
+    const int r8 = lane & 7, mq = lane >> 3;
+    const uint32_t a_hi = isr::smem_u32(dah) + 2u * (uint32_t)((mt * 16 + (mq & 1) * 8 + r8) * WT_DR + (mq >> 1) * 8);
+    const uint32_t a_lo = a_hi + 2u * (uint32_t)(CH * WT_DR);
+    // transposed B blocks: matrix mq = (positions +8 if mq odd, tap +1 if mq >= 2)
+    const uint32_t b_row = isr::smem_u32(xs) + 2u * (uint32_t)(((mq >> 1) + (mq & 1) * 8 + r8) * TC_XR + ci0);
+    float acc[KT][4];
+#pragma unroll
+    for (int k = 0; k < KT; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[k][q] = 0.f;
+    const int span_end = min(L, (int)(blockIdx.x + 1) * WT_SPAN);
+    for (int p0 = blockIdx.x * WT_SPAN; p0 < span_end; p0 += TC_CT) {
+        __syncthreads();   // the previous chunk's tiles are consumed (and db_s is initialised)
+        // gradient: word (co, pp) = positions p0 + 2 pp, +1 of channel co (zero past the span);
+        // the 32 lanes of a warp share co, so the bias gradient reduces per warp first
+        for (int e = tid; e < CH * TC_CT / 2; e += 256) {
+            const int co = e / (TC_CT / 2), pp = e - co * (TC_CT / 2);
+            const int pos = p0 + 2 * pp;
+            const float* src = da + ((size_t)b * CH + co) * L;
+            const float v0 = pos < span_end ? src[pos] : 0.f;
+            const float v1 = pos + 1 < span_end ? src[pos + 1] : 0.f;
+            uint32_t hi, lo;
+            isr::split2<true>(v0, v1, hi, lo);
+            dah[co * (WT_DR / 2) + pp] = hi;
+            dal[co * (WT_DR / 2) + pp] = lo;
+            float s = v0 + v1;
+            for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) atomicAdd(&db_s[co], s);
+        }
+        // activations: position-major tile of positions p0 - 4 + j (zero outside the row)
+        for (int w = tid; w < TC_XW * (CH / 2); w += 256) {
+            const int grp = w >> 5, l = w & 31;
+            const int j = (grp >> 2) * 8 + (l & 7), cp = (grp & 3) * 4 + (l >> 3);
+            const int pos = p0 - HALF + j;
+            const size_t o = ((size_t)b * CH + 2 * cp) * L + pos;
+            const bool inside = pos >= 0 && pos < L;
+            const unsigned short* src = reinterpret_cast<const unsigned short*>(h);
+            const uint32_t v0 = inside ? src[o] : 0u, v1 = inside ? src[o + L] : 0u;
+            xs[j * (TC_XR / 2) + cp] = v0 | (v1 << 16);
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int s = 0; s < TC_CT / 16; ++s) {   // k-step: positions p0 + 16 s ..
+            uint32_t ah[4], al[4];
+            ldsm_x4(ah, a_hi + 2u * (uint32_t)(16 * s));
+            ldsm_x4(al, a_lo + 2u * (uint32_t)(16 * s));
+            const uint4 fh = make_uint4(ah[0], ah[1], ah[2], ah[3]), fl = make_uint4(al[0], al[1], al[2], al[3]);
+#pragma unroll
+            for (int tp = 0; tp < KT - 1; tp += 2) {
+                uint32_t bq[4];
+                ldsm_x4_trans(bq, b_row + 2u * (uint32_t)((16 * s + tp) * TC_XR));
+                isr::mma16816<true>(acc[tp], fh, bq[0], bq[1]);
+                isr::mma16816<true>(acc[tp], fl, bq[0], bq[1]);
+                isr::mma16816<true>(acc[tp + 1], fh, bq[2], bq[3]);
+                isr::mma16816<true>(acc[tp + 1], fl, bq[2], bq[3]);
+            }
+            uint32_t b8[2];   // tap 8: matrices 0 and 1 only (lanes 0-15 give the rows)
+            ldsm_x2_trans(b8, b_row + 2u * (uint32_t)((16 * s + KT - 1 - (mq >> 1)) * TC_XR));
+            isr::mma16816<true>(acc[KT - 1], fh, b8[0], b8[1]);
+            isr::mma16816<true>(acc[KT - 1], fl, b8[0], b8[1]);
+        }
+    }
+    // accumulator (k, q): output channel 16 mt + g + 8 (q >= 2), input channel ci0 + 2 t + (q & 1)
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int k = 0; k < KT; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int co = mt * 16 + g + (q >> 1) * 8, ci = ci0 + 2 * t4 + (q & 1);
+            atomicAdd(&dW[((size_t)co * CH + ci) * KT + k], acc[k][q]);
+        }
+    __syncthreads();
+    if (tid < CH) atomicAdd(&db[tid], db_s[tid]);
 }
 
 // dW[co][ci][k] += sum_i da[b][co][i] h[b][ci][i + k - 4];  db[co] += sum_i da[b][co][i]
@@ -244,23 +519,88 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const TH* __restrict__ h, co
     }
 }
 
-// ---------------------------------------------------------------- head
-// per row: z, max/argmax/mean per channel, presence MLP
-template <class T>
-__global__ void __launch_bounds__(256) head_fwd_kernel(const T* __restrict__ h4, const float* __restrict__ theta, int L,
-                                                       float* __restrict__ z, int* __restrict__ amax,
-                                                       float* __restrict__ pooled, float* __restrict__ u,
-                                                       float* __restrict__ q)
+// ---------------------------------------------------------------- first layer (one input channel)
+// h1[b][co][i] = relu(b1[co] + sum_k W1[co][k] x[b][i + k - 4]).  A thread takes two adjacent
+// positions and loops over the channels, so every channel row is written in coalesced pairs.
+constexpr int L1_CT = 512;   // positions per CTA
+
+template <class T> __device__ __forceinline__ void store_pair(T* o, float a, float b);
+template <> __device__ __forceinline__ void store_pair<float>(float* o, float a, float b)
 {
-    const int b = blockIdx.x;
+    *reinterpret_cast<float2*>(o) = make_float2(a, b);
+}
+template <> __device__ __forceinline__ void store_pair<__nv_bfloat16>(__nv_bfloat16* o, float a, float b)
+{
+    *reinterpret_cast<__nv_bfloat162*>(o) = __floats2bfloat162_rn(a, b);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) conv1_kernel(const T* __restrict__ x, const T* __restrict__ w1,
+                                                    const float* __restrict__ b1, int L, T* __restrict__ out)
+{
+    __shared__ float xs[L1_CT + KT - 1];
+    __shared__ __align__(16) float ws[CH][12];   // W1[co][0..8], b1[co], 0, 0
+    const int b = blockIdx.y, i0 = blockIdx.x * L1_CT;
+    const T* xb = x + (size_t)b * L;
+    for (int j = threadIdx.x; j < L1_CT + KT - 1; j += 256) {
+        const int pos = i0 - HALF + j;
+        xs[j] = (pos >= 0 && pos < L) ? ld<T>(xb, pos) : 0.f;
+    }
+    for (int e = threadIdx.x; e < CH * 12; e += 256) {
+        const int co = e / 12, k = e - co * 12;
+        ws[co][k] = k < KT ? ld<T>(w1, (size_t)k * CH + co) : (k == KT ? b1[co] : 0.f);   // w1: [k][co]
+    }
+    __syncthreads();
+    const int p = 2 * threadIdx.x, i = i0 + p;
+    if (i >= L) return;
+    float xv[KT + 1];
+#pragma unroll
+    for (int j = 0; j < KT + 1; ++j) xv[j] = xs[p + j];
+    const bool pair = i + 1 < L && (L & 1) == 0;   // even row offsets: aligned pair stores
+#pragma unroll 4
+    for (int co = 0; co < CH; ++co) {
+        const float4 wa = *reinterpret_cast<const float4*>(&ws[co][0]);
+        const float4 wb = *reinterpret_cast<const float4*>(&ws[co][4]);
+        const float4 wc = *reinterpret_cast<const float4*>(&ws[co][8]);
+        const float w[KT] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w, wc.x};
+        float s0 = wc.y, s1 = wc.y;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            s0 = fmaf(w[k], xv[k], s0);
+            s1 = fmaf(w[k], xv[k + 1], s1);
+        }
+        s0 = fmaxf(s0, 0.f);
+        s1 = fmaxf(s1, 0.f);
+        T* o = out + ((size_t)b * CH + co) * L + i;
+        if (pair) {
+            store_pair<T>(o, s0, s1);
+        } else {
+            o[0] = cvt<T>(s0);
+            if (i + 1 < L) o[1] = cvt<T>(s1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- head
+// Forward head in two kernels.  head_chunk_kernel: CTA (chunk x of HD_CT positions, row b)
+// writes z for its positions and, per channel, the chunk's max, first arg-max and sum.
+// head_mlp_kernel: per row, the chunk partials -> max / arg-max (first index) / mean per
+// channel, then the presence MLP.
+constexpr int HD_CT = 512;
+
+template <class T>
+__global__ void __launch_bounds__(256) head_chunk_kernel(const T* __restrict__ h4, const float* __restrict__ theta,
+                                                         int L, int nx, float* __restrict__ z,
+                                                         float* __restrict__ pmax, int* __restrict__ pidx,
+                                                         float* __restrict__ psum)
+{
+    const int b = blockIdx.y, xc = blockIdx.x, i0 = xc * HD_CT, iend = min(L, i0 + HD_CT);
     const T* hb = h4 + (size_t)b * CH * L;
     __shared__ float w5[CH];
-    __shared__ float pool_s[2 * CH];
-    __shared__ float u_s[CH];
     if (threadIdx.x < CH) w5[threadIdx.x] = theta[OFF_W5 + threadIdx.x];
     __syncthreads();
     const float b5 = theta[OFF_B5];
-    for (int i = threadIdx.x; i < L; i += 256) {
+    for (int i = i0 + threadIdx.x; i < iend; i += 256) {
         float s = b5;
 #pragma unroll 8
         for (int c = 0; c < CH; ++c) s = fmaf(w5[c], ld<T>(hb, (size_t)c * L + i), s);
@@ -271,9 +611,9 @@ __global__ void __launch_bounds__(256) head_fwd_kernel(const T* __restrict__ h4,
     for (int cc = 0; cc < 4; ++cc) {
         const int c = warp * 4 + cc;
         float mx = -INFINITY, sum = 0.f;
-        int mi = 0;
-        for (int i = lane; i < L; i += 32) {
-            float v = ld<T>(hb, (size_t)c * L + i);
+        int mi = i0;
+        for (int i = i0 + lane; i < iend; i += 32) {
+            const float v = ld<T>(hb, (size_t)c * L + i);
             if (v > mx) {
                 mx = v;
                 mi = i;
@@ -281,8 +621,8 @@ __global__ void __launch_bounds__(256) head_fwd_kernel(const T* __restrict__ h4,
             sum += v;
         }
         for (int o = 16; o; o >>= 1) {
-            float om = __shfl_down_sync(0xffffffffu, mx, o);
-            int oi = __shfl_down_sync(0xffffffffu, mi, o);
+            const float om = __shfl_down_sync(0xffffffffu, mx, o);
+            const int oi = __shfl_down_sync(0xffffffffu, mi, o);
             sum += __shfl_down_sync(0xffffffffu, sum, o);
             if (om > mx || (om == mx && oi < mi)) {
                 mx = om;
@@ -290,10 +630,38 @@ __global__ void __launch_bounds__(256) head_fwd_kernel(const T* __restrict__ h4,
             }
         }
         if (lane == 0) {
-            pool_s[c] = mx;
-            pool_s[CH + c] = sum / L;
-            amax[b * CH + c] = mi;
+            const size_t o = ((size_t)b * nx + xc) * CH + c;
+            pmax[o] = mx;
+            pidx[o] = mi;
+            psum[o] = sum;
         }
+    }
+}
+
+__global__ void __launch_bounds__(64) head_mlp_kernel(const float* __restrict__ theta, int L, int nx,
+                                                      const float* __restrict__ pmax, const int* __restrict__ pidx,
+                                                      const float* __restrict__ psum, int* __restrict__ amax,
+                                                      float* __restrict__ pooled, float* __restrict__ u,
+                                                      float* __restrict__ q)
+{
+    const int b = blockIdx.x;
+    __shared__ float pool_s[2 * CH];
+    __shared__ float u_s[CH];
+    if (threadIdx.x < CH) {
+        const int c = threadIdx.x;
+        float mx = -INFINITY, sum = 0.f;
+        int mi = 0;
+        for (int xc = 0; xc < nx; ++xc) {   // chunks in position order: ties keep the first
+            const size_t o = ((size_t)b * nx + xc) * CH + c;
+            if (pmax[o] > mx) {
+                mx = pmax[o];
+                mi = pidx[o];
+            }
+            sum += psum[o];
+        }
+        pool_s[c] = mx;
+        pool_s[CH + c] = sum / L;
+        amax[b * CH + c] = mi;
     }
     __syncthreads();
     if (threadIdx.x < CH) {
@@ -483,9 +851,13 @@ struct isr_est {
     int64_t step = 0;
     void* wf = nullptr;       // forward working weights (storage type)
     void* wb = nullptr;       // backward-data working weights
+    void* tf = nullptr;       // tensor-core GEMM rows of the forward weights (BF16 only)
+    void* tb = nullptr;       // ... and of the backward-data weights
     void* act[5] = {};        // x, h1..h4 (storage type)
     float *z = nullptr, *pooled = nullptr, *u = nullptr, *q = nullptr, *loss = nullptr;
     int* amax = nullptr;
+    float *pmax = nullptr, *psum = nullptr;   // head partials per (row, chunk, channel)
+    int* pidx = nullptr;
     float *da0 = nullptr, *da1 = nullptr; // gradient ping-pong [B][32][L]
 };
 
@@ -521,6 +893,14 @@ isr_status set_smem_attrs()
     EST_TRY(cudaFuncSetAttribute(conv_kernel<T, T, T, T, CH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     EST_TRY(cudaFuncSetAttribute(conv_kernel<float, T, float, T, CH, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    if constexpr (kTensorConv<T>) {
+        EST_TRY(cudaFuncSetAttribute(conv_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tc_smem_bytes(true)));
+        EST_TRY(cudaFuncSetAttribute(conv_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tc_smem_bytes(false)));
+        EST_TRY(cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)wgrad_tc_smem_bytes()));
+    }
     return ISR_OK;
 }
 
@@ -533,16 +913,24 @@ isr_status forward_t(isr_est* e, const float* x, int n)
     for (int i = 0; i < 5; ++i) act[i] = static_cast<T*>(e->act[i]);
     const size_t nx = (size_t)n * L;
     cast_kernel<T><<<(unsigned)std::min<size_t>((nx + 255) / 256, 4096), 256, 0, s>>>(x, nx, act[0]);
-    relayout_kernel<T><<<(CH * KT + 3 * CH * CH * KT + 255) / 256, 256, 0, s>>>(e->theta, static_cast<T*>(e->wf),
-                                                                                 static_cast<T*>(e->wb));
+    relayout_kernel<T><<<(CH * KT + 3 * CH * CH * KT + 255) / 256, 256, 0, s>>>(
+        e->theta, static_cast<T*>(e->wf), static_cast<T*>(e->wb), static_cast<T*>(e->tf), static_cast<T*>(e->tb));
     const T* wf = static_cast<const T*>(e->wf);
     dim3 grid((L + CT - 1) / CT, n);
-    conv_kernel<T, T, T, T, 1, true><<<grid, 256, conv_smem_bytes(1), s>>>(act[0], wf, e->theta + OFF_B1, nullptr,
-                                                                            L, act[1]);
-    for (int l = 2; l <= 4; ++l)
-        conv_kernel<T, T, T, T, CH, true><<<grid, 256, conv_smem_bytes(CH), s>>>(act[l - 1], wf + CH * KT + (size_t)(l - 2) * CH * CH * KT,
-                                                              e->theta + b_off(l), nullptr, L, act[l]);
-    head_fwd_kernel<T><<<n, 256, 0, s>>>(act[4], e->theta, L, e->z, e->amax, e->pooled, e->u, e->q);
+    conv1_kernel<T><<<dim3((L + L1_CT - 1) / L1_CT, n), 256, 0, s>>>(act[0], wf, e->theta + OFF_B1, L, act[1]);
+    for (int l = 2; l <= 4; ++l) {
+        if constexpr (kTensorConv<T>) {
+            conv_tc_kernel<true><<<dim3((L + TC_CT - 1) / TC_CT, n), 256, tc_smem_bytes(true), s>>>(
+                act[l - 1], static_cast<const T*>(e->tf) + (size_t)(l - 2) * CH * CH * KT, e->theta + b_off(l),
+                nullptr, L, act[l]);
+        } else {
+            conv_kernel<T, T, T, T, CH, true><<<grid, 256, conv_smem_bytes(CH), s>>>(
+                act[l - 1], wf + CH * KT + (size_t)(l - 2) * CH * CH * KT, e->theta + b_off(l), nullptr, L, act[l]);
+        }
+    }
+    const int nxh = (L + HD_CT - 1) / HD_CT;
+    head_chunk_kernel<T><<<dim3(nxh, n), 256, 0, s>>>(act[4], e->theta, L, nxh, e->z, e->pmax, e->pidx, e->psum);
+    head_mlp_kernel<<<n, 64, 0, s>>>(e->theta, L, nxh, e->pmax, e->pidx, e->psum, e->amax, e->pooled, e->u, e->q);
     EST_TRY(cudaGetLastError());
     return ISR_OK;
 }
@@ -567,10 +955,18 @@ isr_status backward_t(isr_est* e, int n, const float* fpos, const float* pres)
         if (l == 1) {
             wgrad_kernel<T, 1><<<gw, 256, 0, s>>>(act[0], da, L, e->grad + OFF_W1, e->grad + OFF_B1);
         } else {
-            wgrad_kernel<T, CH><<<gw, 256, 0, s>>>(act[l - 1], da, L, e->grad + w_off(l), e->grad + b_off(l));
+            if constexpr (kTensorConv<T>)
+                wgrad_tc_kernel<<<dim3((L + WT_SPAN - 1) / WT_SPAN, n), 256, wgrad_tc_smem_bytes(), s>>>(
+                    act[l - 1], da, L, e->grad + w_off(l), e->grad + b_off(l));
+            else
+                wgrad_kernel<T, CH><<<gw, 256, 0, s>>>(act[l - 1], da, L, e->grad + w_off(l), e->grad + b_off(l));
             // gradient into the layer below, masked by its ReLU: da_{l-1} = (W_l^T * da_l) (h_{l-1} > 0)
-            conv_kernel<float, T, float, T, CH, false><<<gc, 256, conv_smem_bytes(CH), s>>>(
-                da, wbk + (size_t)(l - 2) * CH * CH * KT, nullptr, act[l - 1], L, dn);
+            if constexpr (kTensorConv<T>)
+                conv_tc_kernel<false><<<dim3((L + TC_CT - 1) / TC_CT, n), 256, tc_smem_bytes(false), s>>>(
+                    da, static_cast<const T*>(e->tb) + (size_t)(l - 2) * CH * CH * KT, nullptr, act[l - 1], L, dn);
+            else
+                conv_kernel<float, T, float, T, CH, false><<<gc, 256, conv_smem_bytes(CH), s>>>(
+                    da, wbk + (size_t)(l - 2) * CH * CH * KT, nullptr, act[l - 1], L, dn);
             std::swap(da, dn);
         }
     }
@@ -633,6 +1029,10 @@ isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t 
     A((void**)&e->grad, 4 * NPARAM);
     A(&e->wf, es * (CH * KT + 3 * CH * CH * KT));
     A(&e->wb, es * 3 * CH * CH * KT);
+    if (precision == ISR_EST_BF16) {
+        A(&e->tf, es * 3 * CH * CH * KT);
+        A(&e->tb, es * 3 * CH * CH * KT);
+    }
     A(&e->act[0], es * B * L);
     for (int i = 1; i < 5; ++i) A(&e->act[i], es * B * CH * L);
     A((void**)&e->z, 4 * B * L);
@@ -641,6 +1041,10 @@ isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t 
     A((void**)&e->q, 4 * B);
     A((void**)&e->loss, 4);
     A((void**)&e->amax, 4 * B * CH);
+    const size_t nxh = (L + HD_CT - 1) / HD_CT;
+    A((void**)&e->pmax, 4 * B * nxh * CH);
+    A((void**)&e->pidx, 4 * B * nxh * CH);
+    A((void**)&e->psum, 4 * B * nxh * CH);
     A((void**)&e->da0, 4 * B * CH * L);
     A((void**)&e->da1, 4 * B * CH * L);
     if (r == cudaSuccess) r = cudaMemset(e->theta, 0, 4 * NPARAM);
@@ -753,8 +1157,9 @@ void isr_est_destroy(isr_est* e)
     if (!e) return;
     Dev guard(e->dev);
     cudaStreamSynchronize(e->stream);
-    void* ptrs[] = {e->theta, e->m, e->v, e->grad, e->wf, e->wb, e->act[0], e->act[1], e->act[2], e->act[3],
-                    e->act[4], e->z, e->pooled, e->u, e->q, e->loss, e->amax, e->da0, e->da1};
+    void* ptrs[] = {e->theta, e->m, e->v, e->grad, e->wf, e->wb, e->tf, e->tb, e->act[0], e->act[1], e->act[2], e->act[3],
+                    e->act[4], e->z, e->pooled, e->u, e->q, e->loss, e->amax, e->da0, e->da1,
+                    e->pmax, e->pidx, e->psum};
     for (void* p : ptrs) cudaFree(p);
     cudaGetLastError();
     delete e;

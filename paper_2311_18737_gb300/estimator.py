@@ -228,6 +228,27 @@ def evaluate(est: Estimator, data, pf_threshold: float):
     return out
 
 
+def conv_flop(band_len: int) -> float:
+    """Multiply-add FLOP of the four convolutions per spectrum (2 per product)."""
+    return 2.0 * band_len * (C * K + 3 * C * C * K)
+
+
+def predict_rate(est: Estimator, x, band_len: int, reps: int = 5):
+    """Inference rate of isr_est_predict on device-resident features, timed with CUDA events
+    on the estimator's stream after one warm-up pass; the convolutions are ~99 % of its FLOP."""
+    est.predict(x)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(est.stream)
+    for _ in range(reps):
+        est.predict(x)
+    ev1.record(est.stream)
+    ev1.synchronize()
+    s = ev0.elapsed_time(ev1) / 1e3 / reps
+    n = int(x.shape[0])
+    return {"predict_spectra": n, "predict_seconds": s, "predict_spectra_per_s": n / s,
+            "predict_conv_tflops": conv_flop(band_len) * n / s / 1e12}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train-integrations", type=int, default=200)
@@ -241,11 +262,24 @@ def main():
     ap.add_argument("--save-params", default=None)
     ap.add_argument("--net-band", choices=["band", "full"], default="band",
                     help="network input: the 1-15 MHz band or all nfft bins")
+    ap.add_argument("--bench-predict", type=int, default=0, metavar="SPECTRA",
+                    help="only time inference on this many seeded standard-normal feature rows")
     a = ap.parse_args()
     prec = isr.ISR_EST_BF16 if a.precision == "bf16" else isr.ISR_EST_FP32
     lo, ln = (BAND_LO, BAND_LEN) if a.net_band == "band" else (0, NFFT)
     est = Estimator(max_batch=a.batch, precision=prec, band_lo=lo, band_len=ln)
     est.set_params(init_params(0))
+    if a.bench_predict > 0:
+        g = torch.Generator(device=est.dev)
+        g.manual_seed(0)
+        x = torch.randn((a.bench_predict, ln), generator=g, device=est.dev)
+        res = predict_rate(est, x, ln)
+        res.update({"precision": a.precision, "batch": a.batch, "net_band": [lo, lo + ln]})
+        print(json.dumps(res, indent=1))
+        if a.out:
+            with open(a.out, "w") as fh:
+                json.dump(res, fh, indent=1)
+        return
     t0 = time.time()
     tr = make_dataset(a.train_integrations, seed=1, n_ipp=a.n_ipp, est=est)
     te = make_dataset(a.eval_integrations, seed=2, n_ipp=a.n_ipp, est=est)
@@ -256,6 +290,7 @@ def main():
     torch.cuda.synchronize()
     t_train = time.time() - t0
     res = evaluate(est, te, presence_threshold(tr))
+    res.update(predict_rate(est, te["x"], ln))
     res.update({"train_spectra": int(tr["x"].shape[0]), "eval_spectra": int(te["x"].shape[0]), "n_ipp": a.n_ipp,
                 "steps": a.steps, "batch": a.batch, "precision": a.precision, "net_band": [lo, lo + ln],
                 "data_seconds": t_data,

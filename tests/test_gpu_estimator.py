@@ -1,6 +1,7 @@
 """The learned estimator's kernels (through the C ABI) against the FP64 reference:
-features, loss and every parameter's gradient (FP32 storage), the BF16 variant, the
-prediction, and a short end-to-end training on spectra the integrator produces."""
+features, loss and every parameter's gradient (FP32 storage), the BF16 variant (tensor-core
+convolutions) against the reference with BF16 storage rounding, the prediction, and a short
+end-to-end training on spectra the integrator produces."""
 import numpy as np
 import pytest
 import torch
@@ -48,6 +49,51 @@ def test_bf16_storage_close_to_reference():
     assert abs(loss - rl) <= 3e-2 * abs(rl)
     cos = float(g @ rg / (np.linalg.norm(g) * np.linalg.norm(rg)))
     assert cos > 0.98, cos
+    e.close()
+
+
+def _dyadic_case(B=4, L=600, seed=7):
+    """Conv weights and biases in multiples of 1/8 within [-1/4, 1/4] and inputs in multiples
+    of 1/4: every product and FP32 partial sum of the convolutions is exact, so the BF16
+    variant's activations are the BF16 roundings of exact values on both sides.  L = 600 spans
+    two full 256-position tiles of the tensor-core convolution and a ragged third."""
+    rng = np.random.default_rng(seed)
+    d = ref.unpack(ref.init_params(seed))
+    for l in range(1, 5):
+        d[f"W{l}"] = rng.integers(-2, 3, d[f"W{l}"].shape) / 8.0
+        d[f"b{l}"] = rng.integers(-2, 3, d[f"b{l}"].shape) / 8.0
+    theta = ref.pack(d).astype(np.float32)
+    x = (rng.integers(-8, 9, (B, L)) / 4.0).astype(np.float32)
+    f = rng.uniform(3, L - 3, B).astype(np.float32)
+    y = np.array([1, 0, 1, 1][:B], dtype=np.float32)
+    e = est_mod.Estimator(max_batch=8, precision=isr.ISR_EST_BF16, nfft=1024, band_lo=0, band_len=L)
+    e.set_params(theta)
+    dev = torch.device("cuda:0")
+    return e, theta, x, f, y, [torch.from_numpy(a).to(dev) for a in (x, f, y)]
+
+
+def test_bf16_tensor_core_forward_matches_bf16_storage_reference():
+    e, theta, x, f, y, (xd, fd, yd) = _dyadic_case()
+    pos, pres = e.predict(xd)
+    rpos, rpres = ref.predict(theta.astype(np.float64), x, store=ref.round_bf16)
+    assert np.abs(pos.cpu().numpy() - rpos).max() <= 1e-3
+    assert np.abs(pres.cpu().numpy() - rpres).max() <= 1e-5
+    e.close()
+
+
+def test_bf16_tensor_core_gradients_match_bf16_storage_reference():
+    """The backward-data convolution splits the FP32 gradient into two BF16 parts (~16
+    significant bits): every parameter block within 1e-3 of its largest gradient."""
+    e, theta, x, f, y, (xd, fd, yd) = _dyadic_case(seed=8)
+    loss, g = e.grad(xd, fd, yd)
+    rl, rg = ref.loss_and_grad(theta.astype(np.float64), x, f, y, store=ref.round_bf16)
+    assert abs(loss - rl) <= 1e-4 * abs(rl)
+    gd, rd = ref.unpack(g.astype(np.float64)), ref.unpack(rg)
+    gmax = np.abs(rg).max()
+    for name, _ in ref.SHAPES:
+        scale = max(np.abs(rd[name]).max(), 1e-3 * gmax)
+        err = np.abs(gd[name] - rd[name]).max() / scale
+        assert err <= 1e-3, f"{name}: max error {err:.2e} of the block's largest gradient"
     e.close()
 
 
