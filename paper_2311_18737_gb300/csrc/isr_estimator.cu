@@ -224,6 +224,83 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr)
                  : "r"(addr));
 }
 
+// Position-major staging of one row's 32 channels, positions i0 - 4 + j for j < TC_XW (zero
+// outside [0, L)): xs[j][c] at a TC_XR-element pitch.  With L a multiple of 8 every channel row
+// is read in 16-byte pieces along the positions (lane = channel, so the 2-byte shared stores of
+// a warp fill 64 contiguous bytes); otherwise two channels per 32-bit word, element by element.
+__device__ __forceinline__ void stage_act_tile(const unsigned short* __restrict__ rows, int L, int i0,
+                                               unsigned short* xs)
+{
+    if ((L & 7) == 0) {
+        // pieces v cover positions i0 - 8 + 8 v .. +7, v < TC_XW / 8 + 1
+        for (int e = threadIdx.x; e < CH * (TC_XW / 8 + 1); e += blockDim.x) {
+            const int c = e & (CH - 1), v = e / CH;
+            const int pos0 = i0 - 8 + 8 * v;
+            const unsigned short* src = rows + (size_t)c * L;
+            unsigned short t[8];
+            if (pos0 >= 0 && pos0 + 8 <= L) {
+                const uint4 q = *reinterpret_cast<const uint4*>(src + pos0);
+                const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    t[2 * k] = (unsigned short)(w[k] & 0xffffu);
+                    t[2 * k + 1] = (unsigned short)(w[k] >> 16);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) t[k] = (pos0 + k >= 0 && pos0 + k < L) ? src[pos0 + k] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int j = 8 * v - HALF + k;
+                if (j >= 0 && j < TC_XW) xs[j * TC_XR + c] = t[k];
+            }
+        }
+    } else {
+        uint32_t* xw = reinterpret_cast<uint32_t*>(xs);
+        for (int w = threadIdx.x; w < TC_XW * (CH / 2); w += blockDim.x) {
+            const int grp = w >> 5, l = w & 31;
+            const int j = (grp >> 2) * 8 + (l & 7), cp = (grp & 3) * 4 + (l >> 3);
+            const int pos = i0 - HALF + j;
+            const size_t o = (size_t)(2 * cp) * L + pos;
+            const bool inside = pos >= 0 && pos < L;
+            const uint32_t v0 = inside ? rows[o] : 0u, v1 = inside ? rows[o + L] : 0u;
+            xw[j * (TC_XR / 2) + cp] = v0 | (v1 << 16);
+        }
+    }
+}
+
+// The same tile from FP32 rows, split into BF16 hi and lo tiles (with L a multiple of 4, read
+// in 16-byte pieces; positions i0 - 4 + 4 v .. +3, v < TC_XW / 4).
+__device__ __forceinline__ void stage_split_tile(const float* __restrict__ rows, int L, int i0, unsigned short* xh,
+                                                 unsigned short* xl)
+{
+    for (int e = threadIdx.x; e < CH * (TC_XW / 4); e += blockDim.x) {
+        const int c = e & (CH - 1), v = e / CH;
+        const int pos0 = i0 - HALF + 4 * v;
+        const float* src = rows + (size_t)c * L;
+        float t[4];
+        if ((L & 3) == 0 && pos0 >= 0 && pos0 + 4 <= L) {
+            const float4 q = *reinterpret_cast<const float4*>(src + pos0);
+            t[0] = q.x; t[1] = q.y; t[2] = q.z; t[3] = q.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) t[k] = (pos0 + k >= 0 && pos0 + k < L) ? src[pos0 + k] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k += 2) {
+            uint32_t hi, lo;
+            isr::split2<true>(t[k], t[k + 1], hi, lo);
+            const int j = 4 * v + k;
+            xh[j * TC_XR + c] = (unsigned short)(hi & 0xffffu);
+            xh[(j + 1) * TC_XR + c] = (unsigned short)(hi >> 16);
+            xl[j * TC_XR + c] = (unsigned short)(lo & 0xffffu);
+            xl[(j + 1) * TC_XR + c] = (unsigned short)(lo >> 16);
+        }
+    }
+}
+static_assert(TC_XW % 8 == 0, "staging pieces tile the halo'd window");
+
 // FWD: in = BF16 activations [B][32][L], out = BF16 relu(conv + bias).
 // !FWD: in = FP32 gradient [B][32][L], out = FP32 conv masked by mask > 0 (BF16 activations
 // of the layer below), no bias.
@@ -247,27 +324,13 @@ __global__ void __launch_bounds__(256) conv_tc_kernel(const void* __restrict__ i
         const int co = e / (TC_K / 8), q = e - co * (TC_K / 8);
         ws[co * (TC_WR / 8) + q] = w4[e];
     }
-    // input: word (j, cp) holds channels 2 cp and 2 cp + 1 at position i0 - 4 + j; a warp
-    // takes 8 positions x 4 channel pairs, so its stores hit 32 distinct banks
-    for (int w = tid; w < TC_XW * (CH / 2); w += 256) {
-        const int grp = w >> 5, l = w & 31;
-        const int j = (grp >> 2) * 8 + (l & 7), cp = (grp & 3) * 4 + (l >> 3);
-        const int pos = i0 - HALF + j;
-        const size_t o = ((size_t)b * CH + 2 * cp) * L + pos;
-        const bool inside = pos >= 0 && pos < L;
-        if constexpr (FWD) {
-            const unsigned short* src = reinterpret_cast<const unsigned short*>(in);
-            const uint32_t v0 = inside ? src[o] : 0u, v1 = inside ? src[o + L] : 0u;
-            xs[j * (TC_XR / 2) + cp] = v0 | (v1 << 16);
-        } else {
-            const float* src = static_cast<const float*>(in);
-            const float v0 = inside ? src[o] : 0.f, v1 = inside ? src[o + L] : 0.f;
-            uint32_t hi, lo;
-            isr::split2<true>(v0, v1, hi, lo);
-            xs[j * (TC_XR / 2) + cp] = hi;
-            xs[XWORDS + j * (TC_XR / 2) + cp] = lo;
-        }
-    }
+    // input: position-major tile of positions i0 - 4 + j (FP32 input: hi and lo tiles)
+    if constexpr (FWD)
+        stage_act_tile(static_cast<const unsigned short*>(in) + (size_t)b * CH * L, L, i0,
+                       reinterpret_cast<unsigned short*>(xs));
+    else
+        stage_split_tile(static_cast<const float*>(in) + (size_t)b * CH * L, L, i0,
+                         reinterpret_cast<unsigned short*>(xs), reinterpret_cast<unsigned short*>(xs + XWORDS));
     __syncthreads();
 
     float acc[2][4][4];
@@ -364,12 +427,13 @@ __device__ __forceinline__ void ldsm_x2_trans(uint32_t (&r)[2], uint32_t addr)
 // transposed (ldmatrix.trans) from the position-major activation tile of the forward kernel,
 // whose rows i + k start on 16-byte boundaries for every tap k.  CTA: WT_SPAN positions of one
 // row in chunks of TC_CT; warp w: output channels 16 (w % 2) .., input channels 8 (w / 2) ..
-// at all 9 taps; the CTA's partial dW and db are added with one atomic per element.
+// at all 9 taps; the CTA's partial dW and db are added with one atomic per element.  Four
+// CTAs per SM (64 registers, 55 KB of shared memory each) hide the staging loads.
 constexpr int WT_SPAN = 1024;
 constexpr int WT_DR = TC_CT + 8;   // bf16 per staged gradient row (528 B)
 constexpr size_t wgrad_tc_smem_bytes() { return (size_t)2 * (2 * CH * WT_DR + TC_XW * TC_XR); }
 
-__global__ void __launch_bounds__(256) wgrad_tc_kernel(const __nv_bfloat16* __restrict__ h, const float* __restrict__ da,
+__global__ void __launch_bounds__(256, 4) wgrad_tc_kernel(const __nv_bfloat16* __restrict__ h, const float* __restrict__ da,
                                                        int L, float* __restrict__ dW, float* __restrict__ db)
 {
     extern __shared__ __align__(16) unsigned char wt_smem[];
@@ -410,16 +474,8 @@ __global__ void __launch_bounds__(256) wgrad_tc_kernel(const __nv_bfloat16* __re
             if (lane == 0) atomicAdd(&db_s[co], s);
         }
         // activations: position-major tile of positions p0 - 4 + j (zero outside the row)
-        for (int w = tid; w < TC_XW * (CH / 2); w += 256) {
-            const int grp = w >> 5, l = w & 31;
-            const int j = (grp >> 2) * 8 + (l & 7), cp = (grp & 3) * 4 + (l >> 3);
-            const int pos = p0 - HALF + j;
-            const size_t o = ((size_t)b * CH + 2 * cp) * L + pos;
-            const bool inside = pos >= 0 && pos < L;
-            const unsigned short* src = reinterpret_cast<const unsigned short*>(h);
-            const uint32_t v0 = inside ? src[o] : 0u, v1 = inside ? src[o + L] : 0u;
-            xs[j * (TC_XR / 2) + cp] = v0 | (v1 << 16);
-        }
+        stage_act_tile(reinterpret_cast<const unsigned short*>(h) + (size_t)b * CH * L, L, p0,
+                       reinterpret_cast<unsigned short*>(xs));
         __syncthreads();
 #pragma unroll 2
         for (int s = 0; s < TC_CT / 16; ++s) {   // k-step: positions p0 + 16 s ..

@@ -72,8 +72,10 @@ def _dyadic_case(B=4, L=600, seed=7):
     return e, theta, x, f, y, [torch.from_numpy(a).to(dev) for a in (x, f, y)]
 
 
-def test_bf16_tensor_core_forward_matches_bf16_storage_reference():
-    e, theta, x, f, y, (xd, fd, yd) = _dyadic_case()
+# 600: two full 256-position tiles and a ragged third; 37: odd (unpaired stores), one partial tile
+@pytest.mark.parametrize("L", [600, 37])
+def test_bf16_tensor_core_forward_matches_bf16_storage_reference(L):
+    e, theta, x, f, y, (xd, fd, yd) = _dyadic_case(L=L)
     pos, pres = e.predict(xd)
     rpos, rpres = ref.predict(theta.astype(np.float64), x, store=ref.round_bf16)
     assert np.abs(pos.cpu().numpy() - rpos).max() <= 1e-3
@@ -81,10 +83,11 @@ def test_bf16_tensor_core_forward_matches_bf16_storage_reference():
     e.close()
 
 
-def test_bf16_tensor_core_gradients_match_bf16_storage_reference():
+@pytest.mark.parametrize("L", [600, 37])
+def test_bf16_tensor_core_gradients_match_bf16_storage_reference(L):
     """The backward-data convolution splits the FP32 gradient into two BF16 parts (~16
     significant bits): every parameter block within 1e-3 of its largest gradient."""
-    e, theta, x, f, y, (xd, fd, yd) = _dyadic_case(seed=8)
+    e, theta, x, f, y, (xd, fd, yd) = _dyadic_case(L=L, seed=8)
     loss, g = e.grad(xd, fd, yd)
     rl, rg = ref.loss_and_grad(theta.astype(np.float64), x, f, y, store=ref.round_bf16)
     assert abs(loss - rl) <= 1e-4 * abs(rl)
