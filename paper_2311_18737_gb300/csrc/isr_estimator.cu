@@ -758,18 +758,23 @@ __device__ __forceinline__ float block_max(float v, float* red)
     return t;
 }
 
-// per row: loss, dz -> da4 (ReLU-masked gradient of h4), head parameter gradients
-template <class T>
-__global__ void __launch_bounds__(256) head_bwd_kernel(const T* __restrict__ h4, const float* __restrict__ theta, int L,
-                                                       int B, const float* __restrict__ z, const int* __restrict__ amax,
-                                                       const float* __restrict__ pooled, const float* __restrict__ u,
-                                                       const float* __restrict__ q, const float* __restrict__ fpos,
-                                                       const float* __restrict__ pres, float* __restrict__ da4,
-                                                       float* __restrict__ grad, float* __restrict__ loss)
+// Head backward in two kernels.  head_bwd_row_kernel (per row): softmax statistics of z, the
+// loss, the presence-MLP gradients and d(pooled); it leaves per row the scalars the location
+// term needs (lse, 1 / sum t, y / B for gates with a line else 0, the line position) and
+// d(pooled).  head_bwd_chunk_kernel (CTA = HD_CT positions of one row): dz, the ReLU-masked
+// gradient of h4 and the CTA's partial dw5, db5.
+constexpr int HB_SCAL = 4;   // per-row scalars: lse, 1 / sum t, y / B (0 without a line), f
+
+__global__ void __launch_bounds__(256) head_bwd_row_kernel(const float* __restrict__ theta, int L, int B,
+                                                           const float* __restrict__ z, const float* __restrict__ pooled,
+                                                           const float* __restrict__ u, const float* __restrict__ q,
+                                                           const float* __restrict__ fpos, const float* __restrict__ pres,
+                                                           float* __restrict__ scal, float* __restrict__ dpool,
+                                                           float* __restrict__ grad, float* __restrict__ loss)
 {
     const int b = blockIdx.x;
     __shared__ float red[8];
-    __shared__ float w5[CH], dpool[2 * CH], du_s[CH];
+    __shared__ float du_s[CH];
     const float* zb = z + (size_t)b * L;
     const float y = pres[b], f = fpos[b];
     // softmax statistics and target normalisation
@@ -792,13 +797,20 @@ __global__ void __launch_bounds__(256) head_bwd_kernel(const T* __restrict__ h4,
     const float qb = q[b];
     const float sig = 1.f / (1.f + __expf(-qb));
     const float dq = (sig - y) * invB;
-    if (threadIdx.x < CH) w5[threadIdx.x] = theta[OFF_W5 + threadIdx.x];
+    // the location term exists only for gates with a line (its target may lie anywhere,
+    // even outside the band, for gates without one)
+    const bool loc = y > 0.f && st > 0.f;
     if (threadIdx.x == 0) {
         // CE = lse - sum t z / sum t ; BCE in the stable form
-        const float ce = (y > 0.f && st > 0.f) ? y * (lse - stz / st) : 0.f;
+        const float ce = loc ? y * (lse - stz / st) : 0.f;
         const float bce = fmaxf(qb, 0.f) - qb * y + log1pf(__expf(-fabsf(qb)));
         atomicAdd(loss, (bce + ce) * invB);
         atomicAdd(&grad[OFF_BB], dq);
+        float* sc = scal + (size_t)b * HB_SCAL;
+        sc[0] = lse;
+        sc[1] = loc ? 1.f / st : 0.f;
+        sc[2] = loc ? y * invB : 0.f;
+        sc[3] = f;
     }
     // presence MLP backward (threads 0..31)
     if (threadIdx.x < CH) {
@@ -814,38 +826,59 @@ __global__ void __launch_bounds__(256) head_bwd_kernel(const T* __restrict__ h4,
     if (threadIdx.x < 2 * CH) {
         float s = 0.f;
         for (int j = 0; j < CH; ++j) s = fmaf(du_s[j], theta[OFF_WA + j * 2 * CH + threadIdx.x], s);
-        dpool[threadIdx.x] = s;
+        dpool[(size_t)b * 2 * CH + threadIdx.x] = s;
     }
-    __syncthreads();
-    // dz, dw5, db5, da4
-    const T* hb = h4 + (size_t)b * CH * L;
-    float dw5[CH];
+}
+
+// warp w: channels 4w .. 4w+3 of the chunk, lanes along the positions (each warp evaluates dz
+// itself), so a thread keeps four partial dw5 sums and every warp adds its own channels
+template <class T>
+__global__ void __launch_bounds__(256) head_bwd_chunk_kernel(const T* __restrict__ h4, const float* __restrict__ theta,
+                                                             int L, const float* __restrict__ z,
+                                                             const int* __restrict__ amax,
+                                                             const float* __restrict__ scal,
+                                                             const float* __restrict__ dpool, float* __restrict__ da4,
+                                                             float* __restrict__ grad)
+{
+    const int b = blockIdx.y, i0 = blockIdx.x * HD_CT, iend = min(L, i0 + HD_CT);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float* sc = scal + (size_t)b * HB_SCAL;
+    const float lse = sc[0], inv_st = sc[1], ys = sc[2], f = sc[3];
+    float w5[4], gmean[4], gmax[4];
+    int am[4];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) dw5[c] = 0.f;
-    float db5 = 0.f;
-    // the location term exists only for gates with a line (its target may lie anywhere,
-    // even outside the band, for gates without one)
-    const bool loc = y > 0.f && st > 0.f;
-    const float inv_st = loc ? 1.f / st : 0.f;
-    for (int i = threadIdx.x; i < L; i += 256) {
+    for (int cc = 0; cc < 4; ++cc) {
+        const int c = warp * 4 + cc;
+        w5[cc] = theta[OFF_W5 + c];
+        gmax[cc] = dpool[(size_t)b * 2 * CH + c];
+        gmean[cc] = dpool[(size_t)b * 2 * CH + CH + c] / L;
+        am[cc] = amax[b * CH + c];
+    }
+    const float* zb = z + (size_t)b * L;
+    const T* hb = h4 + ((size_t)b * CH + warp * 4) * L;
+    float* ob = da4 + ((size_t)b * CH + warp * 4) * L;
+    float dw5[4] = {0.f, 0.f, 0.f, 0.f}, db5 = 0.f;
+    for (int i = i0 + lane; i < iend; i += 32) {
         const float d = (i - f) / SIGMA_T;
-        const float t = loc ? __expf(-0.5f * d * d) * inv_st : 0.f;
-        const float dz = loc ? y * (__expf(zb[i] - lse) - t) * invB : 0.f;
+        const float dz = ys != 0.f ? ys * (__expf(zb[i] - lse) - __expf(-0.5f * d * d) * inv_st) : 0.f;
         db5 += dz;
 #pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            const float hv = ld<T>(hb, (size_t)c * L + i);
-            dw5[c] = fmaf(dz, hv, dw5[c]);
-            float g = w5[c] * dz + dpool[CH + c] / L;
-            if (i == amax[b * CH + c]) g += dpool[c];
-            da4[((size_t)b * CH + c) * L + i] = hv > 0.f ? g : 0.f;
+        for (int cc = 0; cc < 4; ++cc) {
+            const float hv = ld<T>(hb, (size_t)cc * L + i);
+            dw5[cc] = fmaf(dz, hv, dw5[cc]);
+            float g = w5[cc] * dz + gmean[cc];
+            if (i == am[cc]) g += gmax[cc];
+            ob[(size_t)cc * L + i] = hv > 0.f ? g : 0.f;
         }
     }
-    db5 = block_sum(db5, red);
-    if (threadIdx.x == 0) atomicAdd(&grad[OFF_B5], db5);
-    for (int c = 0; c < CH; ++c) {
-        float s = block_sum(dw5[c], red);
-        if (threadIdx.x == 0) atomicAdd(&grad[OFF_W5 + c], s);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc)
+        for (int o = 16; o; o >>= 1) dw5[cc] += __shfl_down_sync(0xffffffffu, dw5[cc], o);
+    for (int o = 16; o; o >>= 1) db5 += __shfl_down_sync(0xffffffffu, db5, o);
+    if (lane == 0) {
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) atomicAdd(&grad[OFF_W5 + warp * 4 + cc], dw5[cc]);
+        if (warp == 0) atomicAdd(&grad[OFF_B5], db5);
     }
 }
 
@@ -913,6 +946,7 @@ struct isr_est {
     float *z = nullptr, *pooled = nullptr, *u = nullptr, *q = nullptr, *loss = nullptr;
     int* amax = nullptr;
     float *pmax = nullptr, *psum = nullptr;   // head partials per (row, chunk, channel)
+    float *hscal = nullptr, *dpool = nullptr; // head backward: per-row scalars and d(pooled)
     int* pidx = nullptr;
     float *da0 = nullptr, *da1 = nullptr; // gradient ping-pong [B][32][L]
 };
@@ -1000,8 +1034,10 @@ isr_status backward_t(isr_est* e, int n, const float* fpos, const float* pres)
     for (int i = 0; i < 5; ++i) act[i] = static_cast<T*>(e->act[i]);
     EST_TRY(cudaMemsetAsync(e->grad, 0, sizeof(float) * NPARAM, s));
     EST_TRY(cudaMemsetAsync(e->loss, 0, sizeof(float), s));
-    head_bwd_kernel<T><<<n, 256, 0, s>>>(act[4], e->theta, L, n, e->z, e->amax, e->pooled, e->u, e->q, fpos, pres,
-                                         e->da0, e->grad, e->loss);
+    head_bwd_row_kernel<<<n, 256, 0, s>>>(e->theta, L, n, e->z, e->pooled, e->u, e->q, fpos, pres, e->hscal,
+                                          e->dpool, e->grad, e->loss);
+    head_bwd_chunk_kernel<T><<<dim3((L + HD_CT - 1) / HD_CT, n), 256, 0, s>>>(act[4], e->theta, L, e->z, e->amax,
+                                                                              e->hscal, e->dpool, e->da0, e->grad);
     const T* wbk = static_cast<const T*>(e->wb);
     float* da = e->da0;
     float* dn = e->da1;
@@ -1101,6 +1137,8 @@ isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t 
     A((void**)&e->pmax, 4 * B * nxh * CH);
     A((void**)&e->pidx, 4 * B * nxh * CH);
     A((void**)&e->psum, 4 * B * nxh * CH);
+    A((void**)&e->hscal, 4 * B * HB_SCAL);
+    A((void**)&e->dpool, 4 * B * 2 * CH);
     A((void**)&e->da0, 4 * B * CH * L);
     A((void**)&e->da1, 4 * B * CH * L);
     if (r == cudaSuccess) r = cudaMemset(e->theta, 0, 4 * NPARAM);
@@ -1215,7 +1253,7 @@ void isr_est_destroy(isr_est* e)
     cudaStreamSynchronize(e->stream);
     void* ptrs[] = {e->theta, e->m, e->v, e->grad, e->wf, e->wb, e->tf, e->tb, e->act[0], e->act[1], e->act[2], e->act[3],
                     e->act[4], e->z, e->pooled, e->u, e->q, e->loss, e->amax, e->da0, e->da1,
-                    e->pmax, e->pidx, e->psum};
+                    e->pmax, e->pidx, e->psum, e->hscal, e->dpool};
     for (void* p : ptrs) cudaFree(p);
     cudaGetLastError();
     delete e;
