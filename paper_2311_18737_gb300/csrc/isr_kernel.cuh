@@ -746,7 +746,7 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
         }
         // ---- pass A: decode, radix-M DFT over stride 1024, DIF twiddles, scatter to regions;
         // butterflies b and b + 1 of a thread are the adjacent columns n, n + 1
-        float2 zp[M];
+        float2 zp[M] = {};   // even butterflies fill it before the odd ones read it
         static_for<BF>([&](auto Bc) {
             constexpr int b = decltype(Bc)::value;
             const int n = 2 * (t + T * (b >> 1)) + (b & 1);
