@@ -78,3 +78,97 @@ def test_fp32_peak_rejects_bad_arguments_on_host():
     assert lib.isr_fp32_peak(0, 0, None, None) == isr.ISR_ERR_INVALID_ARG
     tf, ms = ctypes.c_double(), ctypes.c_double()
     assert lib.isr_fp32_peak(0, 2, ctypes.byref(tf), ctypes.byref(ms)) == isr.ISR_ERR_INVALID_ARG
+
+
+def _status(fn, *args, msg=None):
+    """Status of a call that must fail; msg: a fragment its error text must contain (so that
+    the intended check, not an earlier one, fired)."""
+    with pytest.raises(isr.IsrError) as ei:
+        fn(*args)
+    text = isr.isr_last_error()
+    assert text
+    if msg is not None:
+        assert msg in text, text
+    return ei.value.status
+
+
+FAKE = 0x10000   # a non-NULL address; every call below fails its host checks before using it
+
+
+def test_peak_fit_rejects_bad_arguments_on_host():
+    lib = isr.load_library()
+    assert lib.isr_peak_fit(None, 4, 1024, 0, 10, None, None, None) == isr.ISR_ERR_INVALID_ARG
+    for n_ranges, nfft, lo, hi in [(0, 1024, 0, 10), (4, 4, 0, 2), (4, 1024, 10, 10), (4, 1024, -1, 10),
+                                   (4, 1024, 0, 1025)]:
+        assert _status(isr.isr_peak_fit, FAKE, n_ranges, nfft, lo, hi, FAKE, FAKE,
+                       msg="band_lo < band_hi") == isr.ISR_ERR_INVALID_ARG
+
+
+def test_estimator_rejects_bad_arguments_on_host():
+    lib = isr.load_library()
+    assert lib.isr_est_create(None, 16384, 320, 4608, 128, isr.ISR_EST_BF16, -1, None) == isr.ISR_ERR_INVALID_ARG
+    for nfft, lo, ln, mb in [(16384, 320, 8, 128), (16384, 16000, 4608, 128), (16384, -1, 4608, 128),
+                             (16384, 320, 4608, 0), (4, 0, 16, 1)]:
+        assert _status(isr.isr_est_create, nfft, lo, ln, mb, msg="band_len >= 16") == isr.ISR_ERR_INVALID_ARG
+    assert _status(isr.isr_est_create, 16384, 320, 4608, 128, 9, msg="precision") == isr.ISR_ERR_UNSUPPORTED
+    assert lib.isr_est_set_params(None, None) == isr.ISR_ERR_INVALID_ARG
+    assert lib.isr_est_get_params(None, None) == isr.ISR_ERR_INVALID_ARG
+    assert lib.isr_est_features(None, None, 1, None) == isr.ISR_ERR_INVALID_ARG
+    assert lib.isr_est_predict(None, None, 1, None, None) == isr.ISR_ERR_INVALID_ARG
+    assert lib.isr_est_grad(None, None, 1, None, None, None, None) == isr.ISR_ERR_INVALID_ARG
+    assert lib.isr_est_train_step(None, None, 1, None, None, 1e-3, None) == isr.ISR_ERR_INVALID_ARG
+    lib.isr_est_destroy(None)  # NULL is safe
+
+
+def _window(**kw):
+    w = isr.IsrWindow()
+    w.echo, w.tx_code, w.out = FAKE, FAKE, FAKE
+    w.echo_stride, w.tx_stride, w.nfft, w.code_len = 8192, 0, 4096, 4096
+    w.n_ranges, w.range_start, w.range_step, w.n_ipp, w.order, w.reserved = 10, 0, 25, 100, -1, 0
+    for k, v in kw.items():
+        setattr(w, k, v)
+    return w
+
+
+@pytest.mark.parametrize("kw,status,msg", [
+    (dict(nfft=1024, code_len=1024), isr.ISR_ERR_UNSUPPORTED, "nfft"),     # batched windows: nfft 2048..16384
+    (dict(nfft=3000), isr.ISR_ERR_UNSUPPORTED, "nfft"),
+    (dict(code_len=0), isr.ISR_ERR_INVALID_ARG, "geometry"),
+    (dict(n_ipp=0), isr.ISR_ERR_INVALID_ARG, "geometry"),
+    (dict(echo_stride=8190), isr.ISR_ERR_INVALID_ARG, "geometry"),
+    (dict(order=9), isr.ISR_ERR_INVALID_ARG, "geometry"),
+    (dict(tx_stride=100), isr.ISR_ERR_INVALID_ARG, "geometry"),
+    (dict(n_ranges=200), isr.ISR_ERR_OUT_OF_RANGE, "past the echo row"),   # 199 * 25 + 4096 > 8192
+    (dict(echo=0), isr.ISR_ERR_INVALID_ARG, "NULL or misaligned"),
+    (dict(echo=FAKE + 4), isr.ISR_ERR_INVALID_ARG, "NULL or misaligned"),  # echo must be 16-byte aligned
+])
+def test_batch_rejects_bad_windows_on_host(kw, status, msg):
+    # windows are checked in order and a good window's device-pointer query needs a GPU, so
+    # the bad window is the only one
+    assert _status(isr.isr_batch_create, [_window(**kw)], msg=msg) == status
+
+
+def test_batch_rejects_bad_calls_on_host():
+    lib = isr.load_library()
+    h = ctypes.c_void_p()
+    arr = (isr.IsrWindow * 1)(_window())
+    assert lib.isr_batch_create(None, arr, 1, 0, -1, None) == isr.ISR_ERR_INVALID_ARG
+    assert lib.isr_batch_create(ctypes.byref(h), None, 1, 0, -1, None) == isr.ISR_ERR_INVALID_ARG
+    assert lib.isr_batch_create(ctypes.byref(h), arr, 0, 0, -1, None) == isr.ISR_ERR_INVALID_ARG
+    assert lib.isr_batch_create(ctypes.byref(h), arr, 1, 64, -1, None) == isr.ISR_ERR_INVALID_ARG   # unknown flag
+    assert lib.isr_batch_run(None) == isr.ISR_ERR_INVALID_ARG
+    assert lib.isr_batch_wait(None) == isr.ISR_ERR_INVALID_ARG
+    assert lib.isr_batch_query(None, None) == isr.ISR_ERR_INVALID_ARG
+    lib.isr_batch_destroy(None)  # NULL is safe
+
+
+def test_allocation_free_call_rejects_bad_arguments_on_host():
+    lib = isr.load_library()
+    assert lib.isr_integrate_static(None, None, None, 1, None) == isr.ISR_ERR_INVALID_ARG
+    assert _status(isr.isr_integrate_static, _desc(nfft=1000), FAKE, FAKE, 1, FAKE,
+                   msg="power of two") == isr.ISR_ERR_UNSUPPORTED
+    assert _status(isr.isr_integrate_static, _desc(n_ranges=50), FAKE, FAKE, 1, FAKE) == isr.ISR_ERR_OUT_OF_RANGE
+    # 4097 gates x 1024 bins exceed the 4 Mi-float static scratch (geometry itself is valid)
+    big = _desc(n_ranges=4097, range_step=1, echo_stride=8192)
+    assert _status(isr.isr_integrate_static, big, FAKE, FAKE, 1, FAKE,
+                   msg="static scratch") == isr.ISR_ERR_INVALID_ARG
