@@ -648,7 +648,8 @@ template <class T>
 __global__ void __launch_bounds__(256) head_chunk_kernel(const T* __restrict__ h4, const float* __restrict__ theta,
                                                          int L, int nx, float* __restrict__ z,
                                                          float* __restrict__ pmax, int* __restrict__ pidx,
-                                                         float* __restrict__ psum)
+                                                         float* __restrict__ psum, float* __restrict__ zmax,
+                                                         int* __restrict__ zidx)
 {
     const int b = blockIdx.y, xc = blockIdx.x, i0 = xc * HD_CT, iend = min(L, i0 + HD_CT);
     const T* hb = h4 + (size_t)b * CH * L;
@@ -656,14 +657,44 @@ __global__ void __launch_bounds__(256) head_chunk_kernel(const T* __restrict__ h
     if (threadIdx.x < CH) w5[threadIdx.x] = theta[OFF_W5 + threadIdx.x];
     __syncthreads();
     const float b5 = theta[OFF_B5];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float zm = -INFINITY;   // the chunk's largest z and its first position
+    int zi = i0;
     for (int i = i0 + threadIdx.x; i < iend; i += 256) {
         float s = b5;
 #pragma unroll 8
         for (int c = 0; c < CH; ++c) s = fmaf(w5[c], ld<T>(hb, (size_t)c * L + i), s);
         z[(size_t)b * L + i] = s;
+        if (s > zm) {
+            zm = s;
+            zi = i;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        const float om = __shfl_down_sync(0xffffffffu, zm, o);
+        const int oi = __shfl_down_sync(0xffffffffu, zi, o);
+        if (om > zm || (om == zm && oi < zi)) {
+            zm = om;
+            zi = oi;
+        }
+    }
+    __shared__ float zm_s[8];
+    __shared__ int zi_s[8];
+    if (lane == 0) {
+        zm_s[warp] = zm;
+        zi_s[warp] = zi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w)
+            if (zm_s[w] > zm_s[0] || (zm_s[w] == zm_s[0] && zi_s[w] < zi_s[0])) {
+                zm_s[0] = zm_s[w];
+                zi_s[0] = zi_s[w];
+            }
+        zmax[(size_t)b * nx + xc] = zm_s[0];
+        zidx[(size_t)b * nx + xc] = zi_s[0];
     }
     // warp w: channels 4w .. 4w+3
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int cc = 0; cc < 4; ++cc) {
         const int c = warp * 4 + cc;
         float mx = -INFINITY, sum = 0.f;
@@ -694,15 +725,37 @@ __global__ void __launch_bounds__(256) head_chunk_kernel(const T* __restrict__ h
     }
 }
 
+// With pos and pres (inference) it also gives the prediction: position = softmax-weighted mean
+// over the 7 bins around the first arg-max of z (+ band_lo), presence = sigmoid(q).
 __global__ void __launch_bounds__(64) head_mlp_kernel(const float* __restrict__ theta, int L, int nx,
                                                       const float* __restrict__ pmax, const int* __restrict__ pidx,
-                                                      const float* __restrict__ psum, int* __restrict__ amax,
-                                                      float* __restrict__ pooled, float* __restrict__ u,
-                                                      float* __restrict__ q)
+                                                      const float* __restrict__ psum, const float* __restrict__ z,
+                                                      const float* __restrict__ zmax, const int* __restrict__ zidx,
+                                                      int lo, int* __restrict__ amax, float* __restrict__ pooled,
+                                                      float* __restrict__ u, float* __restrict__ q,
+                                                      float* __restrict__ pos, float* __restrict__ pres)
 {
     const int b = blockIdx.x;
     __shared__ float pool_s[2 * CH];
     __shared__ float u_s[CH];
+    if (pos && threadIdx.x == CH) {
+        float mx = -INFINITY;
+        int mi = 0;
+        for (int xc = 0; xc < nx; ++xc)   // chunks in position order: ties keep the first
+            if (zmax[(size_t)b * nx + xc] > mx) {
+                mx = zmax[(size_t)b * nx + xc];
+                mi = zidx[(size_t)b * nx + xc];
+            }
+        const float* zb = z + (size_t)b * L;
+        const int a = max(0, mi - WIN), e = min(L, mi + WIN + 1);
+        double sw = 0, swi = 0;
+        for (int i = a; i < e; ++i) {
+            const double wgt = exp((double)zb[i] - (double)mx);
+            sw += wgt;
+            swi += wgt * i;
+        }
+        pos[b] = (float)(lo + swi / sw);
+    }
     if (threadIdx.x < CH) {
         const int c = threadIdx.x;
         float mx = -INFINITY, sum = 0.f;
@@ -733,6 +786,7 @@ __global__ void __launch_bounds__(64) head_mlp_kernel(const float* __restrict__ 
         float s = theta[OFF_BB];
         for (int j = 0; j < CH; ++j) s = fmaf(theta[OFF_WB + j], u_s[j], s);
         q[b] = s;
+        if (pres) pres[b] = 1.f / (1.f + expf(-s));
     }
 }
 
@@ -895,42 +949,6 @@ __global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__
     }
 }
 
-// per row: position = softmax-weighted mean over the 7 bins around argmax z (+ band_lo),
-// presence = sigmoid(q)
-__global__ void predict_kernel(const float* __restrict__ z, const float* __restrict__ q, int L, int lo,
-                               float* __restrict__ pos, float* __restrict__ pres)
-{
-    const int b = blockIdx.x;
-    const float* zb = z + (size_t)b * L;
-    float mx = -INFINITY;
-    int mi = 0;
-    for (int i = threadIdx.x; i < L; i += 32) {
-        if (zb[i] > mx) {
-            mx = zb[i];
-            mi = i;
-        }
-    }
-    for (int o = 16; o; o >>= 1) {
-        float om = __shfl_down_sync(0xffffffffu, mx, o);
-        int oi = __shfl_down_sync(0xffffffffu, mi, o);
-        if (om > mx || (om == mx && oi < mi)) {
-            mx = om;
-            mi = oi;
-        }
-    }
-    if (threadIdx.x == 0) {
-        const int a = max(0, mi - WIN), e = min(L, mi + WIN + 1);
-        double sw = 0, swi = 0;
-        for (int i = a; i < e; ++i) {
-            const double wgt = exp((double)zb[i] - (double)mx);
-            sw += wgt;
-            swi += wgt * i;
-        }
-        pos[b] = (float)(lo + swi / sw);
-        pres[b] = 1.f / (1.f + expf(-q[b]));
-    }
-}
-
 }  // namespace
 
 struct isr_est {
@@ -947,6 +965,9 @@ struct isr_est {
     int* amax = nullptr;
     float *pmax = nullptr, *psum = nullptr;   // head partials per (row, chunk, channel)
     float *hscal = nullptr, *dpool = nullptr; // head backward: per-row scalars and d(pooled)
+    float* zmax = nullptr;                    // per (row, chunk): largest location logit ...
+    int* zidx = nullptr;                      // ... and its first position
+    bool weights_stale = true;                // the working weights need the master copy's values
     int* pidx = nullptr;
     float *da0 = nullptr, *da1 = nullptr; // gradient ping-pong [B][32][L]
 };
@@ -994,8 +1015,9 @@ isr_status set_smem_attrs()
     return ISR_OK;
 }
 
+// pos / pres: the prediction outputs (inference), or NULL
 template <class T>
-isr_status forward_t(isr_est* e, const float* x, int n)
+isr_status forward_t(isr_est* e, const float* x, int n, float* pos = nullptr, float* pres = nullptr)
 {
     const int L = e->L;
     cudaStream_t s = e->stream;
@@ -1003,8 +1025,11 @@ isr_status forward_t(isr_est* e, const float* x, int n)
     for (int i = 0; i < 5; ++i) act[i] = static_cast<T*>(e->act[i]);
     const size_t nx = (size_t)n * L;
     cast_kernel<T><<<(unsigned)std::min<size_t>((nx + 255) / 256, 4096), 256, 0, s>>>(x, nx, act[0]);
-    relayout_kernel<T><<<(CH * KT + 3 * CH * CH * KT + 255) / 256, 256, 0, s>>>(
-        e->theta, static_cast<T*>(e->wf), static_cast<T*>(e->wb), static_cast<T*>(e->tf), static_cast<T*>(e->tb));
+    if (e->weights_stale) {   // working weights follow the master copy only after it changed
+        relayout_kernel<T><<<(CH * KT + 3 * CH * CH * KT + 255) / 256, 256, 0, s>>>(
+            e->theta, static_cast<T*>(e->wf), static_cast<T*>(e->wb), static_cast<T*>(e->tf), static_cast<T*>(e->tb));
+        e->weights_stale = false;
+    }
     const T* wf = static_cast<const T*>(e->wf);
     dim3 grid((L + CT - 1) / CT, n);
     conv1_kernel<T><<<dim3((L + L1_CT - 1) / L1_CT, n), 256, 0, s>>>(act[0], wf, e->theta + OFF_B1, L, act[1]);
@@ -1019,8 +1044,10 @@ isr_status forward_t(isr_est* e, const float* x, int n)
         }
     }
     const int nxh = (L + HD_CT - 1) / HD_CT;
-    head_chunk_kernel<T><<<dim3(nxh, n), 256, 0, s>>>(act[4], e->theta, L, nxh, e->z, e->pmax, e->pidx, e->psum);
-    head_mlp_kernel<<<n, 64, 0, s>>>(e->theta, L, nxh, e->pmax, e->pidx, e->psum, e->amax, e->pooled, e->u, e->q);
+    head_chunk_kernel<T><<<dim3(nxh, n), 256, 0, s>>>(act[4], e->theta, L, nxh, e->z, e->pmax, e->pidx, e->psum,
+                                                      e->zmax, e->zidx);
+    head_mlp_kernel<<<n, 64, 0, s>>>(e->theta, L, nxh, e->pmax, e->pidx, e->psum, e->z, e->zmax, e->zidx, e->lo,
+                                     e->amax, e->pooled, e->u, e->q, pos, pres);
     EST_TRY(cudaGetLastError());
     return ISR_OK;
 }
@@ -1139,6 +1166,8 @@ isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t 
     A((void**)&e->psum, 4 * B * nxh * CH);
     A((void**)&e->hscal, 4 * B * HB_SCAL);
     A((void**)&e->dpool, 4 * B * 2 * CH);
+    A((void**)&e->zmax, 4 * B * nxh);
+    A((void**)&e->zidx, 4 * B * nxh);
     A((void**)&e->da0, 4 * B * CH * L);
     A((void**)&e->da1, 4 * B * CH * L);
     if (r == cudaSuccess) r = cudaMemset(e->theta, 0, 4 * NPARAM);
@@ -1169,6 +1198,7 @@ isr_status isr_est_set_params(isr_est* e, const float* params)
     EST_TRY(cudaMemsetAsync(e->v, 0, 4 * NPARAM, e->stream));
     EST_TRY(cudaStreamSynchronize(e->stream));
     e->step = 0;
+    e->weights_stale = true;
     return ISR_OK;
 }
 
@@ -1225,6 +1255,7 @@ isr_status isr_est_train_step(isr_est* e, const float* x, int32_t n, const float
     const float c1 = 1.f / (1.f - powf(b1, (float)e->step)), c2 = 1.f / (1.f - powf(b2, (float)e->step));
     adam_kernel<<<(NPARAM + 255) / 256, 256, 0, e->stream>>>(e->theta, e->grad, e->m, e->v, NPARAM, lr, b1, b2, 1e-8f,
                                                               c1, c2);
+    e->weights_stale = true;
     EST_TRY(cudaGetLastError());
     if (loss) {
         EST_TRY(cudaMemcpyAsync(loss, e->loss, 4, cudaMemcpyDefault, e->stream));
@@ -1239,11 +1270,8 @@ isr_status isr_est_predict(isr_est* e, const float* x, int32_t n, float* line_bi
     if (st != ISR_OK) return st;
     if (!line_bin || !presence) return fail(ISR_ERR_INVALID_ARG, "outputs must not be NULL");
     Dev guard(e->dev);
-    st = e->precision == ISR_EST_BF16 ? forward_t<__nv_bfloat16>(e, x, n) : forward_t<float>(e, x, n);
-    if (st != ISR_OK) return st;
-    predict_kernel<<<n, 32, 0, e->stream>>>(e->z, e->q, e->L, e->lo, line_bin, presence);
-    EST_TRY(cudaGetLastError());
-    return ISR_OK;
+    return e->precision == ISR_EST_BF16 ? forward_t<__nv_bfloat16>(e, x, n, line_bin, presence)
+                                        : forward_t<float>(e, x, n, line_bin, presence);
 }
 
 void isr_est_destroy(isr_est* e)
@@ -1253,7 +1281,7 @@ void isr_est_destroy(isr_est* e)
     cudaStreamSynchronize(e->stream);
     void* ptrs[] = {e->theta, e->m, e->v, e->grad, e->wf, e->wb, e->tf, e->tb, e->act[0], e->act[1], e->act[2], e->act[3],
                     e->act[4], e->z, e->pooled, e->u, e->q, e->loss, e->amax, e->da0, e->da1,
-                    e->pmax, e->pidx, e->psum, e->hscal, e->dpool};
+                    e->pmax, e->pidx, e->psum, e->hscal, e->dpool, e->zmax, e->zidx};
     for (void* p : ptrs) cudaFree(p);
     cudaGetLastError();
     delete e;
