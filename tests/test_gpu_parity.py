@@ -147,6 +147,30 @@ def test_mean_and_reset_flags():
         assert n == 0 and not host.any()
 
 
+def test_zero_ipps_is_a_no_op():
+    """n_ipp == 0 changes neither the sums nor the IPP count, even with NULL buffers; a
+    negative count is an argument error."""
+    rng = np.random.default_rng(13)
+    nfft, R, P = 1024, 5, 4
+    echo, tx = _rand_case(rng, nfft, R, P, start=0, step=25, L=nfft, kind="pm1", per=False)
+    ref = oracle.integrate(echo, tx, nfft=nfft, n_ranges=R, range_step=25)
+    dev = torch.device("cuda:0")
+    e, t = torch.from_numpy(echo).to(dev), torch.from_numpy(tx).to(dev)
+    with isr.Plan(nfft=nfft, n_ranges=R, echo_stride=echo.shape[1], range_step=25, device=0,
+                  stream=torch.cuda.current_stream()) as plan:
+        isr.isr_integrate(plan.handle, None, None, 0, None, nfft)
+        plan.integrate(e, t, 2)
+        plan.integrate(e, t, 0)
+        isr.isr_integrate(plan.handle, None, None, 0, None, nfft)
+        plan.integrate(e[2:], t, P - 2)
+        with pytest.raises(isr.IsrError) as ei:
+            isr.isr_integrate(plan.handle, e, t, -1, None, nfft)
+        assert ei.value.status == isr.ISR_ERR_INVALID_ARG
+        out, n = plan.spectra()
+    assert n == P
+    assert_parity(out.numpy().astype(np.float64), ref, what="zero-IPP calls")
+
+
 def test_ranges_override():
     rng = np.random.default_rng(12)
     nfft, R, P = 512, 7, 4
