@@ -198,20 +198,24 @@ __global__ void __launch_bounds__(256) conv_kernel(const TIN* __restrict__ in, c
 // 32 distinct banks.  The backward-data convolution is the same GEMM on the flipped transposed
 // weights; its FP32 input (the gradient) is split into two BF16 parts, hi + lo, and both are
 // multiplied, so the products keep ~16 bits of the gradient and the FP32 accumulation.
-// CTA: 256 positions x 32 output channels; warp w: positions [32 w, 32 w + 32), all channels.
-constexpr int TC_CT = 256;                 // positions per CTA
-constexpr int TC_XW = TC_CT + KT - 1;      // staged positions, halo included
+// CTA: CF_CT = 512 positions x 32 output channels, 16 warps; warp w: positions [32 w, 32 w + 32),
+// all channels (a CTA stages the 18 KB of weights once per 512 positions).
+constexpr int CF_CT = 512;                 // positions per convolution CTA
+constexpr int CF_THREADS = 16 * 32;
+constexpr int CF_XW = CF_CT + KT - 1;      // staged positions, halo included
+constexpr int CF_OR = CF_CT + 8;           // output staging row (elements)
+constexpr int TC_CT = 256;                 // positions per weight-gradient chunk
+constexpr int TC_XW = TC_CT + KT - 1;
 constexpr int TC_XR = CH + 8;              // bf16 per staged position (80 B)
 constexpr int TC_K = KT * CH;              // GEMM depth
 constexpr int TC_WR = TC_K + 8;            // bf16 per staged weight row (592 B)
-constexpr int TC_OR = TC_CT + 8;           // output staging row (elements)
 constexpr size_t tc_smem_bytes(bool fwd)
 {
-    return (size_t)2 * ((fwd ? 1 : 2) * TC_XW * TC_XR + CH * TC_WR);
+    return (size_t)2 * ((fwd ? 1 : 2) * CF_XW * TC_XR + CH * TC_WR);
 }
-static_assert(TC_XW * (CH / 2) % 32 == 0, "input staging assigns whole warps");
-static_assert((size_t)CH * TC_OR * 4 <= (size_t)2 * 2 * TC_XW * TC_XR, "FP32 output tile fits the input tiles");
-static_assert((size_t)CH * TC_OR * 2 <= (size_t)2 * TC_XW * TC_XR, "BF16 output tile fits the input tile");
+static_assert(CF_CT == CF_THREADS, "a warp per 32 positions");
+static_assert((size_t)CH * CF_OR * 4 <= (size_t)2 * 2 * CF_XW * TC_XR, "FP32 output tile fits the input tiles");
+static_assert((size_t)CH * CF_OR * 2 <= (size_t)2 * CF_XW * TC_XR, "BF16 output tile fits the input tile");
 
 // BF16 storage runs the 32 -> 32 channel convolutions on the tensor cores
 template <class T> constexpr bool kTensorConv = false;
@@ -224,16 +228,18 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr)
                  : "r"(addr));
 }
 
-// Position-major staging of one row's 32 channels, positions i0 - 4 + j for j < TC_XW (zero
+// Position-major staging of one row's 32 channels, positions i0 - 4 + j for j < XW (zero
 // outside [0, L)): xs[j][c] at a TC_XR-element pitch.  With L a multiple of 8 every channel row
 // is read in 16-byte pieces along the positions (lane = channel, so the 2-byte shared stores of
 // a warp fill 64 contiguous bytes); otherwise two channels per 32-bit word, element by element.
+template <int XW>
 __device__ __forceinline__ void stage_act_tile(const unsigned short* __restrict__ rows, int L, int i0,
                                                unsigned short* xs)
 {
+    static_assert(XW % 8 == 0 && XW * (CH / 2) % 32 == 0, "staging pieces tile the halo'd window");
     if ((L & 7) == 0) {
-        // pieces v cover positions i0 - 8 + 8 v .. +7, v < TC_XW / 8 + 1
-        for (int e = threadIdx.x; e < CH * (TC_XW / 8 + 1); e += blockDim.x) {
+        // pieces v cover positions i0 - 8 + 8 v .. +7, v < XW / 8 + 1
+        for (int e = threadIdx.x; e < CH * (XW / 8 + 1); e += blockDim.x) {
             const int c = e & (CH - 1), v = e / CH;
             const int pos0 = i0 - 8 + 8 * v;
             const unsigned short* src = rows + (size_t)c * L;
@@ -253,12 +259,12 @@ __device__ __forceinline__ void stage_act_tile(const unsigned short* __restrict_
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int j = 8 * v - HALF + k;
-                if (j >= 0 && j < TC_XW) xs[j * TC_XR + c] = t[k];
+                if (j >= 0 && j < XW) xs[j * TC_XR + c] = t[k];
             }
         }
     } else {
         uint32_t* xw = reinterpret_cast<uint32_t*>(xs);
-        for (int w = threadIdx.x; w < TC_XW * (CH / 2); w += blockDim.x) {
+        for (int w = threadIdx.x; w < XW * (CH / 2); w += blockDim.x) {
             const int grp = w >> 5, l = w & 31;
             const int j = (grp >> 2) * 8 + (l & 7), cp = (grp & 3) * 4 + (l >> 3);
             const int pos = i0 - HALF + j;
@@ -271,11 +277,12 @@ __device__ __forceinline__ void stage_act_tile(const unsigned short* __restrict_
 }
 
 // The same tile from FP32 rows, split into BF16 hi and lo tiles (with L a multiple of 4, read
-// in 16-byte pieces; positions i0 - 4 + 4 v .. +3, v < TC_XW / 4).
+// in 16-byte pieces; positions i0 - 4 + 4 v .. +3, v < XW / 4).
+template <int XW>
 __device__ __forceinline__ void stage_split_tile(const float* __restrict__ rows, int L, int i0, unsigned short* xh,
                                                  unsigned short* xl)
 {
-    for (int e = threadIdx.x; e < CH * (TC_XW / 4); e += blockDim.x) {
+    for (int e = threadIdx.x; e < CH * (XW / 4); e += blockDim.x) {
         const int c = e & (CH - 1), v = e / CH;
         const int pos0 = i0 - HALF + 4 * v;
         const float* src = rows + (size_t)c * L;
@@ -299,38 +306,38 @@ __device__ __forceinline__ void stage_split_tile(const float* __restrict__ rows,
         }
     }
 }
-static_assert(TC_XW % 8 == 0, "staging pieces tile the halo'd window");
+
 
 // FWD: in = BF16 activations [B][32][L], out = BF16 relu(conv + bias).
 // !FWD: in = FP32 gradient [B][32][L], out = FP32 conv masked by mask > 0 (BF16 activations
 // of the layer below), no bias.
 template <bool FWD>
-__global__ void __launch_bounds__(256) conv_tc_kernel(const void* __restrict__ in, const __nv_bfloat16* __restrict__ wt,
+__global__ void __launch_bounds__(CF_THREADS) conv_tc_kernel(const void* __restrict__ in, const __nv_bfloat16* __restrict__ wt,
                                                       const float* __restrict__ bias,
                                                       const __nv_bfloat16* __restrict__ mask, int L,
                                                       void* __restrict__ out)
 {
     constexpr int NX = FWD ? 1 : 2;                    // staged input parts
-    constexpr int XWORDS = TC_XW * TC_XR / 2;          // 32-bit words per staged part
+    constexpr int XWORDS = CF_XW * TC_XR / 2;          // 32-bit words per staged part
     extern __shared__ __align__(16) unsigned char tc_smem[];
     uint32_t* xs = reinterpret_cast<uint32_t*>(tc_smem);
     uint4* ws = reinterpret_cast<uint4*>(tc_smem + (size_t)4 * NX * XWORDS);
-    const int b = blockIdx.y, i0 = blockIdx.x * TC_CT;
+    const int b = blockIdx.y, i0 = blockIdx.x * CF_CT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // weights: [co][288] rows, 16-byte copies into 592-byte rows
     const uint4* w4 = reinterpret_cast<const uint4*>(wt);
-    for (int e = tid; e < CH * (TC_K / 8); e += 256) {
+    for (int e = tid; e < CH * (TC_K / 8); e += CF_THREADS) {
         const int co = e / (TC_K / 8), q = e - co * (TC_K / 8);
         ws[co * (TC_WR / 8) + q] = w4[e];
     }
     // input: position-major tile of positions i0 - 4 + j (FP32 input: hi and lo tiles)
     if constexpr (FWD)
-        stage_act_tile(static_cast<const unsigned short*>(in) + (size_t)b * CH * L, L, i0,
-                       reinterpret_cast<unsigned short*>(xs));
+        stage_act_tile<CF_XW>(static_cast<const unsigned short*>(in) + (size_t)b * CH * L, L, i0,
+                              reinterpret_cast<unsigned short*>(xs));
     else
-        stage_split_tile(static_cast<const float*>(in) + (size_t)b * CH * L, L, i0,
-                         reinterpret_cast<unsigned short*>(xs), reinterpret_cast<unsigned short*>(xs + XWORDS));
+        stage_split_tile<CF_XW>(static_cast<const float*>(in) + (size_t)b * CH * L, L, i0,
+                                reinterpret_cast<unsigned short*>(xs), reinterpret_cast<unsigned short*>(xs + XWORDS));
     __syncthreads();
 
     float acc[2][4][4];
@@ -383,23 +390,23 @@ __global__ void __launch_bounds__(256) conv_tc_kernel(const void* __restrict__ i
                 const int pl = warp * 32 + nt * 8 + 2 * t4;
                 const float v0 = acc[mt][nt][2 * h] + bv, v1 = acc[mt][nt][2 * h + 1] + bv;
                 if constexpr (FWD)
-                    reinterpret_cast<uint32_t*>(tc_smem)[(co * TC_OR + pl) / 2] =
+                    reinterpret_cast<uint32_t*>(tc_smem)[(co * CF_OR + pl) / 2] =
                         isr::pack2<true>(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
                 else
-                    reinterpret_cast<float2*>(tc_smem)[(co * TC_OR + pl) / 2] = make_float2(v0, v1);
+                    reinterpret_cast<float2*>(tc_smem)[(co * CF_OR + pl) / 2] = make_float2(v0, v1);
             }
         }
     __syncthreads();
-    // coalesced rows: warp w writes channels w, w + 8, w + 16, w + 24
-    for (int co = warp; co < CH; co += 8) {
+    // coalesced rows: warp w writes channels w and w + 16
+    for (int co = warp; co < CH; co += CF_THREADS / 32) {
         const size_t row = ((size_t)b * CH + co) * L;
-        for (int q = lane; q < TC_CT; q += 32) {
+        for (int q = lane; q < CF_CT; q += 32) {
             const int i = i0 + q;
             if (i >= L) break;
             if constexpr (FWD) {
-                static_cast<__nv_bfloat16*>(out)[row + i] = reinterpret_cast<const __nv_bfloat16*>(tc_smem)[co * TC_OR + q];
+                static_cast<__nv_bfloat16*>(out)[row + i] = reinterpret_cast<const __nv_bfloat16*>(tc_smem)[co * CF_OR + q];
             } else {
-                const float v = reinterpret_cast<const float*>(tc_smem)[co * TC_OR + q];
+                const float v = reinterpret_cast<const float*>(tc_smem)[co * CF_OR + q];
                 static_cast<float*>(out)[row + i] = __bfloat162float(mask[row + i]) > 0.f ? v : 0.f;
             }
         }
@@ -474,8 +481,8 @@ __global__ void __launch_bounds__(256, 4) wgrad_tc_kernel(const __nv_bfloat16* _
             if (lane == 0) atomicAdd(&db_s[co], s);
         }
         // activations: position-major tile of positions p0 - 4 + j (zero outside the row)
-        stage_act_tile(reinterpret_cast<const unsigned short*>(h) + (size_t)b * CH * L, L, p0,
-                       reinterpret_cast<unsigned short*>(xs));
+        stage_act_tile<TC_XW>(reinterpret_cast<const unsigned short*>(h) + (size_t)b * CH * L, L, p0,
+                              reinterpret_cast<unsigned short*>(xs));
         __syncthreads();
 #pragma unroll 2
         for (int s = 0; s < TC_CT / 16; ++s) {   // k-step: positions p0 + 16 s ..
@@ -1035,7 +1042,7 @@ isr_status forward_t(isr_est* e, const float* x, int n, float* pos = nullptr, fl
     conv1_kernel<T><<<dim3((L + L1_CT - 1) / L1_CT, n), 256, 0, s>>>(act[0], wf, e->theta + OFF_B1, L, act[1]);
     for (int l = 2; l <= 4; ++l) {
         if constexpr (kTensorConv<T>) {
-            conv_tc_kernel<true><<<dim3((L + TC_CT - 1) / TC_CT, n), 256, tc_smem_bytes(true), s>>>(
+            conv_tc_kernel<true><<<dim3((L + CF_CT - 1) / CF_CT, n), CF_THREADS, tc_smem_bytes(true), s>>>(
                 act[l - 1], static_cast<const T*>(e->tf) + (size_t)(l - 2) * CH * CH * KT, e->theta + b_off(l),
                 nullptr, L, act[l]);
         } else {
@@ -1081,7 +1088,7 @@ isr_status backward_t(isr_est* e, int n, const float* fpos, const float* pres)
                 wgrad_kernel<T, CH><<<gw, 256, 0, s>>>(act[l - 1], da, L, e->grad + w_off(l), e->grad + b_off(l));
             // gradient into the layer below, masked by its ReLU: da_{l-1} = (W_l^T * da_l) (h_{l-1} > 0)
             if constexpr (kTensorConv<T>)
-                conv_tc_kernel<false><<<dim3((L + TC_CT - 1) / TC_CT, n), 256, tc_smem_bytes(false), s>>>(
+                conv_tc_kernel<false><<<dim3((L + CF_CT - 1) / CF_CT, n), CF_THREADS, tc_smem_bytes(false), s>>>(
                     da, static_cast<const T*>(e->tb) + (size_t)(l - 2) * CH * CH * KT, nullptr, act[l - 1], L, dn);
             else
                 conv_kernel<float, T, float, T, CH, false><<<gc, 256, conv_smem_bytes(CH), s>>>(
