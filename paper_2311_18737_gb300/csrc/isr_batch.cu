@@ -144,8 +144,8 @@ struct RedSeg {
     int chunks;
 };
 
-// out[i] = (float) sum_c part[c][i] in double, one window per blockIdx.y
-// out[i] = sum_c part[c][i], FP32 with Kahan compensation (error ~2 ulp for any chunk count)
+// out[i] = sum_c part[c][i], FP32 with Kahan compensation (error ~2 ulp for any chunk count);
+// one window per blockIdx.y
 __global__ void batch_reduce_kernel(const RedSeg* __restrict__ segs)
 {
     const RedSeg s = segs[blockIdx.y];
@@ -197,6 +197,7 @@ struct isr_batch {
     int order[4] = {0, 0, 0, 0};
     float tune_ms[4][4] = {};
     int64_t transforms = 0;
+    int64_t max_bins = 0;   // largest window's n_ranges x nfft
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -235,8 +236,11 @@ isr_status enqueue(isr_batch* b, int n_units, bool reduce, cudaStream_t s)
     batch_kernel<<<b->sm_count, isr::kThreads, kBatchSmem, s>>>(b->d_wins, b->d_units, n_units, b->counter);
     B_TRY(cudaGetLastError());
     if (reduce) {
-        batch_reduce_kernel<<<dim3((unsigned)std::max(1, 2 * b->sm_count / (int)b->w.size() + 1), (unsigned)b->w.size()),
-                              256, 0, s>>>(b->d_segs);
+        // memory-bound: about four waves of 256-thread CTAs over all windows (8 per SM resident),
+        // at most one CTA per 256 elements of the largest window
+        const int64_t want = (4 * 8 * (int64_t)b->sm_count + (int64_t)b->w.size() - 1) / (int64_t)b->w.size();
+        const int64_t gx = std::max<int64_t>(1, std::min<int64_t>(want, (b->max_bins + 255) / 256));
+        batch_reduce_kernel<<<dim3((unsigned)gx, (unsigned)b->w.size()), 256, 0, s>>>(b->d_segs);
         B_TRY(cudaGetLastError());
     }
     return ISR_OK;
@@ -370,6 +374,7 @@ isr_status isr_batch_create(isr_batch** out, const isr_window* windows, int32_t 
         part_floats += (int64_t)bw.n_cy * w.n_ranges * w.nfft;
         b->hw.push_back(bw);
         b->transforms += (int64_t)w.n_ranges * w.n_ipp;
+        b->max_bins = std::max<int64_t>(b->max_bins, (int64_t)w.n_ranges * w.nfft);
     }
     e = cudaMalloc(&b->partial, sizeof(float) * part_floats);
     if (e == cudaSuccess) e = cudaMalloc(&b->counter, sizeof(int));
