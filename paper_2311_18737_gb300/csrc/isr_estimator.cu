@@ -432,16 +432,28 @@ __device__ __forceinline__ void ldsm_x2_trans(uint32_t (&r)[2], uint32_t addr)
 // the GEMM D[co][kk] = sum_i A[co][i] B[i][kk] with kk = (k, ci), A = da (FP32, split into BF16
 // hi + lo, both multiplied) and B[i][(k, ci)] = h[ci][i + k - 4].  B's 8 x 8 blocks are read
 // transposed (ldmatrix.trans) from the position-major activation tile of the forward kernel,
-// whose rows i + k start on 16-byte boundaries for every tap k.  CTA: WT_SPAN positions of one
+// whose rows i + k start on 16-byte boundaries for every tap k.  CTA: `span` positions of one
 // row in chunks of TC_CT; warp w: output channels 16 (w % 2) .., input channels 8 (w / 2) ..
 // at all 9 taps; the CTA's partial dW and db are added with one atomic per element.  Four
 // CTAs per SM (64 registers, 55 KB of shared memory each) hide the staging loads.
-constexpr int WT_SPAN = 1024;
 constexpr int WT_DR = TC_CT + 8;   // bf16 per staged gradient row (528 B)
 constexpr size_t wgrad_tc_smem_bytes() { return (size_t)2 * (2 * CH * WT_DR + TC_XW * TC_XR); }
 
+// Chunks per CTA for n rows of L positions with `slots` resident CTAs: the shortest span whose
+// CTAs fit in one wave (else one CTA per row).  Every CTA ends with an atomic add to each of the
+// same 9216 weights, so more, shorter CTAs contend there: at 128 rows x 4608 positions 2, 4 and 5
+// chunks per CTA took 235, 195 and 157 us per launch.
+int wgrad_span_chunks(int L, int n, int slots)
+{
+    const int cpr = (L + TC_CT - 1) / TC_CT;
+    for (int k = 1; k <= cpr; ++k)
+        if ((int64_t)n * ((cpr + k - 1) / k) <= slots) return k;
+    return cpr;
+}
+
 __global__ void __launch_bounds__(256, 4) wgrad_tc_kernel(const __nv_bfloat16* __restrict__ h, const float* __restrict__ da,
-                                                       int L, float* __restrict__ dW, float* __restrict__ db)
+                                                       int L, int span, float* __restrict__ dW,
+                                                       float* __restrict__ db)
 {
     extern __shared__ __align__(16) unsigned char wt_smem[];
     uint32_t* dah = reinterpret_cast<uint32_t*>(wt_smem);   // [CH][WT_DR / 2] words, hi parts
@@ -461,8 +473,8 @@ __global__ void __launch_bounds__(256, 4) wgrad_tc_kernel(const __nv_bfloat16* _
     for (int k = 0; k < KT; ++k)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[k][q] = 0.f;
-    const int span_end = min(L, (int)(blockIdx.x + 1) * WT_SPAN);
-    for (int p0 = blockIdx.x * WT_SPAN; p0 < span_end; p0 += TC_CT) {
+    const int span_end = min(L, (int)(blockIdx.x + 1) * span);
+    for (int p0 = blockIdx.x * span; p0 < span_end; p0 += TC_CT) {
         __syncthreads();   // the previous chunk's tiles are consumed (and db_s is initialised)
         // gradient: word (co, pp) = positions p0 + 2 pp, +1 of channel co (zero past the span);
         // the 32 lanes of a warp share co, so the bias gradient reduces per warp first
@@ -975,6 +987,7 @@ struct isr_est {
     float* zmax = nullptr;                    // per (row, chunk): largest location logit ...
     int* zidx = nullptr;                      // ... and its first position
     bool weights_stale = true;                // the working weights need the master copy's values
+    int wgrad_slots = 0;                      // resident tensor-core weight-gradient CTAs (all SMs)
     int* pidx = nullptr;
     float *da0 = nullptr, *da1 = nullptr; // gradient ping-pong [B][32][L]
 };
@@ -1077,13 +1090,14 @@ isr_status backward_t(isr_est* e, int n, const float* fpos, const float* pres)
     float* dn = e->da1;
     dim3 gw((L + WG_SPAN - 1) / WG_SPAN, n);
     dim3 gc((L + CT - 1) / CT, n);
+    const int span = TC_CT * wgrad_span_chunks(L, n, std::max(1, e->wgrad_slots));
     for (int l = 4; l >= 1; --l) {
         if (l == 1) {
             wgrad_kernel<T, 1><<<gw, 256, 0, s>>>(act[0], da, L, e->grad + OFF_W1, e->grad + OFF_B1);
         } else {
             if constexpr (kTensorConv<T>)
-                wgrad_tc_kernel<<<dim3((L + WT_SPAN - 1) / WT_SPAN, n), 256, wgrad_tc_smem_bytes(), s>>>(
-                    act[l - 1], da, L, e->grad + w_off(l), e->grad + b_off(l));
+                wgrad_tc_kernel<<<dim3((L + span - 1) / span, n), 256, wgrad_tc_smem_bytes(), s>>>(
+                    act[l - 1], da, L, span, e->grad + w_off(l), e->grad + b_off(l));
             else
                 wgrad_kernel<T, CH><<<gw, 256, 0, s>>>(act[l - 1], da, L, e->grad + w_off(l), e->grad + b_off(l));
             // gradient into the layer below, masked by its ReLU: da_{l-1} = (W_l^T * da_l) (h_{l-1} > 0)
@@ -1185,6 +1199,13 @@ isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t 
         if (st != ISR_OK) {
             isr_est_destroy(e);
             return st;
+        }
+        if (precision == ISR_EST_BF16) {
+            int sms = 0, occ = 0;
+            r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (r == cudaSuccess)
+                r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wgrad_tc_kernel, 256, wgrad_tc_smem_bytes());
+            e->wgrad_slots = std::max(1, occ) * std::max(1, sms);
         }
     }
     if (r != cudaSuccess) {
