@@ -299,13 +299,14 @@ isr_status integrate_host(isr_plan* p, const int16_t* echo, const void* tx, int6
     const char* txc = static_cast<const char*>(tx);
     bool tx_dev = is_device_ptr(tx);
     // a call larger than one staging buffer starts with a small block, so the kernels get going
-    // after a short copy, then goes on in blocks as large as a buffer (few launches: each launch
-    // ends with a partly filled wave); a call that fits one buffer is one block
-    const int64_t first = n > rows ? std::max<int64_t>(1, std::min<int64_t>(rows, kHostFirstBytes / row_bytes)) : rows;
+    // after a short copy, and the blocks then grow 4x up to a buffer: each copy stays shorter
+    // than the kernels of the block before it even on a slow host link, with few launches
+    // (each ends with a partly filled wave); a call that fits one buffer is one block
+    int64_t cur = n > rows ? std::max<int64_t>(1, std::min<int64_t>(rows, kHostFirstBytes / row_bytes)) : rows;
     int blk = 0;
-    for (int64_t done = 0, nb = 0; done < n; done += nb, ++blk) {
+    for (int64_t done = 0, nb = 0; done < n; done += nb, ++blk, cur = std::min<int64_t>(rows, 4 * cur)) {
         const int b = blk & 1;
-        nb = std::min(blk == 0 ? first : rows, n - done);
+        nb = std::min(cur, n - done);
         CUDA_TRY(cudaStreamWaitEvent(p->copy_stream, p->hs_free[b], 0));
         CUDA_TRY(cudaMemcpyAsync(p->hs_echo[b], echo + done * p->d.echo_stride * 2, (size_t)(nb * row_bytes),
                                  cudaMemcpyHostToDevice, p->copy_stream));

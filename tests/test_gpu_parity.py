@@ -127,6 +127,21 @@ def test_host_resident_input():
     assert_parity(got, ref, what="host input")
 
 
+def test_host_input_larger_than_a_staging_buffer():
+    """Host rows beyond one 1 GiB staging buffer: the library streams them in several blocks
+    through two device buffers (the first block smaller), and the sums equal the oracle's."""
+    rng = np.random.default_rng(21)
+    nfft, R, step = 16384, 3, 25
+    stride = ((R - 1) * step + nfft + 3) // 4 * 4
+    P = (1 << 30) // (stride * 4) + 1200                  # ~1.07 GiB of host rows
+    echo = rng.integers(-3000, 3001, size=(P, stride, 2), dtype=np.int16)
+    tx = np.where(rng.random(nfft) < 0.5, -1, 1).astype(np.int8)
+    ref = oracle.integrate(echo, tx, nfft=nfft, n_ranges=R, range_step=step)
+    got, info = gpu_integrate(echo, tx, nfft=nfft, n_ranges=R, range_step=step, host_input=True)
+    assert info["kernel_launches"] >= 3                 # first block, a full buffer, the rest
+    assert_parity(got, ref, what="host input over several staging blocks")
+
+
 def test_mean_and_reset_flags():
     rng = np.random.default_rng(4)
     nfft, R, P = 256, 9, 6
