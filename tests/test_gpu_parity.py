@@ -61,6 +61,21 @@ def test_code_formats(kind, per, log2n):
     assert_parity(got, ref, what=f"{kind} per={per} nfft={nfft}")
 
 
+# every transform length through the kernels for codes that are not full-length binary phase:
+# a zero-padded +-1 code, a full-length complex int16 code and a zero-padded complex float code
+@pytest.mark.parametrize("kind,padded", [("pm1", True), ("ci16", False), ("c32", True)])
+@pytest.mark.parametrize("log2n", list(range(3, 15)))
+def test_every_nfft_general_codes(log2n, kind, padded):
+    rng = np.random.default_rng(100 + 3 * log2n + len(kind))
+    nfft = 1 << log2n
+    R, P = 3, 3
+    L = nfft - max(1, nfft // 8) if padded else nfft
+    echo, tx = _rand_case(rng, nfft, R, P, start=2, step=5, L=L, kind=kind, per=False)
+    got, _ = gpu_integrate(echo, tx, nfft=nfft, n_ranges=R, range_start=2, range_step=5, code_len=L)
+    ref = oracle.integrate(echo, tx, nfft=nfft, n_ranges=R, range_start=2, range_step=5, code_len=L)
+    assert_parity(got, ref, what=f"{kind} L={L} nfft={nfft}")
+
+
 @pytest.mark.parametrize("order,log2n", [(o, l) for l in (11, 12, 13, 14) for o in range(4)] + [(4, 14), (5, 14)])
 def test_radix_orders(log2n, order):
     rng = np.random.default_rng(31 * log2n + order)
