@@ -76,6 +76,21 @@ def test_every_nfft_general_codes(log2n, kind, padded):
     assert_parity(got, ref, what=f"{kind} L={L} nfft={nfft}")
 
 
+@pytest.mark.parametrize("kind", ["pm1", "ci16"])
+@pytest.mark.parametrize("log2n", [11, 14])
+def test_per_ipp_code_rows_longer_than_the_code(log2n, kind):
+    """Per-IPP code rows 32 chips longer than code_len (tx_stride > code_len): each IPP reads
+    the first code_len chips of its own row; full-length codes, so +-1 codes take the fast kernel."""
+    rng = np.random.default_rng(300 + log2n + len(kind))
+    nfft = 1 << log2n
+    R, P = 3, 5
+    echo, tx = _rand_case(rng, nfft, R, P, start=0, step=9, L=nfft + 32, kind=kind, per=True)
+    echo = np.ascontiguousarray(echo[:, : ((2 * 9 + nfft + 3) // 4 * 4 + 8)])
+    got, _ = gpu_integrate(echo, tx, nfft=nfft, n_ranges=R, range_step=9, code_len=nfft, per_ipp_tx=True)
+    ref = oracle.integrate(echo, tx, nfft=nfft, n_ranges=R, range_step=9, code_len=nfft, per_ipp_tx=True)
+    assert_parity(got, ref, what=f"{kind} tx_stride {nfft + 32} code_len {nfft}")
+
+
 @pytest.mark.parametrize("order,log2n", [(o, l) for l in (11, 12, 13, 14) for o in range(4)] + [(4, 14), (5, 14)])
 def test_radix_orders(log2n, order):
     rng = np.random.default_rng(31 * log2n + order)
