@@ -5,12 +5,17 @@ over all IPPs (decode -> FFT -> |X|^2 accumulate, chunk reduction) followed by
 isr_spectra into a device buffer.  The echo is generated on the device before timing
 (1.66 GB of int16 IQ, larger than L2, so no flush is needed between steps).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--scaling weak|strong]
 
-With N > 1 (under torchrun) every rank integrates its own block of range gates (an
-independent problem of the same size: weak scaling, no data-path collective); rank 0
-prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on host cores on
-a bounded sample of the same workload.
+N > 1 runs one process per GPU under torch.distributed.run (bench.py re-launches itself
+that way when started directly with --gpus N; under a launcher whose world size differs
+from N it exits with status 2).  --scaling weak (default): every rank integrates its own
+problem of the full size (independent gate blocks with their own seeds; no data-path
+collective).  --scaling strong: the ranks split ONE workload's gates into contiguous
+blocks, each rank keeps only the echo samples its gates read, and the [R_g][nfft] blocks
+are gathered to rank 0 at the end of every step.  Rank 0 prints one JSON line.
+``--impl reference`` times the FP64 CPU oracle on host cores on a bounded sample of the
+same workload.
 """
 from __future__ import annotations
 
@@ -151,10 +156,34 @@ def max_over_ranks(values, device, world, use_dist=None):
     return [float(x) for x in t.tolist()]
 
 
-def job_throughput(world, n_ranges, n_ipp, ms):
-    """Whole-job spectra/s: every rank integrates its own n_ranges x n_ipp problem (weak
-    scaling), the job takes the slowest rank's time."""
-    return world * n_ranges * n_ipp / (ms / 1000.0)
+def job_throughput(world, n_ranges, n_ipp, ms, strong=False):
+    """Whole-job spectra/s; the job takes the slowest rank's time.  Weak scaling: every rank
+    integrates its own n_ranges x n_ipp problem.  Strong scaling: n_ranges is the one
+    workload's gate count, split over the ranks."""
+    return (1 if strong else world) * n_ranges * n_ipp / (ms / 1000.0)
+
+
+def world_check(gpus, world, launched):
+    """What to do with --gpus N given the launcher's world size: "run" (they agree),
+    "relaunch" (started directly with N > 1: re-run under torch.distributed.run) or "error"
+    (a launcher started a different number of ranks)."""
+    if gpus < 1:
+        return "error"
+    if gpus == world:
+        return "run"
+    if world == 1 and not launched and gpus > 1:
+        return "relaunch"
+    return "error"
+
+
+def _relaunch(gpus):
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
 
 
 def _cpu_sample(w, n_gates, n_ipp, threads):
@@ -222,6 +251,8 @@ def run_ours(args):
     import synth
     from paper_2311_18737_gb300 import isr
 
+    from paper_2311_18737_gb300 import shard
+
     world, rank, local = _dist()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
@@ -233,15 +264,29 @@ def run_ours(args):
     if use_dist:
         dist.init_process_group("nccl", device_id=dev)
 
-    w = _workload(args.workload, rank, args.n_ranges, args.n_ipp)
-    R, N, P = w.n_ranges, w.nfft, w.n_ipp
+    strong = args.scaling == "strong"
+    # strong scaling: one workload (rank 0's seed) split by gates; weak: a problem per rank
+    w = _workload(args.workload, 0 if strong else rank, args.n_ranges, args.n_ipp)
+    R_total, N, P = w.n_ranges, w.nfft, w.n_ipp
     echo = torch.empty((P, w.echo_stride, 2), dtype=torch.int16, device=dev)
     code_d = torch.from_numpy(w.code()).to(dev)
     w.echo_device(echo.data_ptr(), code_d.data_ptr())
+    R, range_start, echo_stride = R_total, w.range_start, w.echo_stride
+    blocks = [(0, R_total)]
+    if strong:
+        blocks = shard.gate_blocks(R_total, world)
+        first, R = blocks[rank]
+        if R < 1:
+            raise SystemExit(f"--scaling strong: {world} ranks for {R_total} gates leaves rank {rank} without gates")
+        span = shard.echo_span(first, R, w.range_start, w.range_step, w.code_len)
+        # this rank keeps only the echo samples its gates read
+        echo = echo[:, span["s0"]:span["s0"] + span["echo_stride"], :].contiguous()
+        range_start, echo_stride = span["range_start"], span["echo_stride"]
+        torch.cuda.empty_cache()
     stream = torch.cuda.Stream(dev)
     out = torch.empty((R, N), dtype=torch.float32, device=dev)
 
-    plan = isr.Plan(nfft=N, n_ranges=R, echo_stride=w.echo_stride, range_start=w.range_start,
+    plan = isr.Plan(nfft=N, n_ranges=R, echo_stride=echo_stride, range_start=range_start,
                     range_step=w.range_step, tx_type=isr.ISR_TX_PM1, device=local, stream=stream)
     # radix order: time the candidates on a probe of the workload and keep the fastest
     if args.order is not None:
@@ -253,9 +298,19 @@ def run_ours(args):
         tune = plan.autotune(echo, code_d, min(P, 512))
     plan.set_profiling(True)
 
+    gathered = {}
+
     def step(e, c, o):
         plan.integrate(e, c, P)
-        plan.spectra(o, isr.ISR_RESET_AFTER)
+        if strong and use_dist:
+            plan.spectra(out, isr.ISR_RESET_AFTER)
+            with torch.cuda.stream(stream):
+                g = shard.gather_gate_blocks(out, blocks, rank, world)
+            if g is not None and o is not out:
+                o.copy_(g, non_blocking=True)
+            gathered["last"] = g
+        else:
+            plan.spectra(o, isr.ISR_RESET_AFTER)
 
     for _ in range(max(3, args.warmup)):
         step(echo, code_d, out)
@@ -293,7 +348,7 @@ def run_ours(args):
         echo_h = torch.empty(echo.shape, dtype=torch.int16, pin_memory=True)
         echo_h.copy_(echo)
         code_h = code_d.cpu().pin_memory()
-        out_h = torch.empty((R, N), dtype=torch.float32, pin_memory=True)
+        out_h = torch.empty((R_total if (strong and rank == 0) else R, N), dtype=torch.float32, pin_memory=True)
         step(echo_h, code_h, out_h)
         torch.cuda.synchronize(dev)
         if use_dist:
@@ -303,7 +358,7 @@ def run_ours(args):
             step(echo_h, code_h, out_h)
         e2e_ms = 1000 * (time.perf_counter() - t0) / args.e2e_steps
         e2e_ms = max_over_ranks([e2e_ms], dev, world, use_dist)[0]
-        e2e = {"value": job_throughput(world, R, P, e2e_ms), "unit": UNIT,
+        e2e = {"value": job_throughput(world, R_total if strong else R, P, e2e_ms, strong), "unit": UNIT,
                "h2d_bytes_per_step": int(echo_h.numel() * 2 + code_h.numel()),
                "d2h_bytes_per_step": int(out_h.numel() * 4), "ms_per_step": e2e_ms}
         del echo_h
@@ -327,12 +382,14 @@ def run_ours(args):
                     "how": "isr_fp32_peak: FMA-only kernel, 8 independent chains per thread, 4 x 256 threads "
                            "per SM, best of 3 runs; ffma2 = paired FP32 instruction"}
 
-    line = {"metric": METRIC, "value": job_throughput(world, R, P, ms), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+    line = {"metric": METRIC, "value": job_throughput(world, R_total if strong else R, P, ms, strong), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "strong" if strong else "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded Philox echoes generated on the device, not timed)",
             "config": {"workload": _workload_desc(w), "nfft": N, "n_ranges": R, "n_ipp": P,
-                       "gates_per_rank": R, "l2": "inputs larger than L2 (echo %.2f GB per step)" % (
+                       "gates_per_rank": R, "partition": ("contiguous gate blocks, echo sub-span per rank, "
+                                                           "blocks gathered to rank 0 each step") if strong else
+                       "independent problem per rank", "l2": "inputs larger than L2 (echo %.2f GB per step)" % (
                            echo.numel() * 2 / 1e9), "kernel": "fused decode+FFT+|X|^2, chunks of %d IPPs" %
                        plan.info()["ipp_chunk"], "radix_order": tune["order"], "radix_order_probe_ms": tune["ms"],
                        "realtime_factor_at_10ms_ipp": (P * 0.010) / (ms / 1000)},
@@ -392,6 +449,8 @@ def _recorded_traffic(nfft, n_ranges, n_ipp, order):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--scaling", choices=["weak", "strong"], default="weak",
+                    help="weak: a full problem per rank; strong: one workload split by gates")
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -407,6 +466,14 @@ def main():
     ap.add_argument("--n-ranges", type=int, default=None, help="resize the workload (profiling cases)")
     ap.add_argument("--n-ipp", type=int, default=None, help="resize the workload (profiling cases)")
     args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    launched = "TORCHELASTIC_RUN_ID" in os.environ or "RANK" in os.environ
+    action = world_check(args.gpus, world, launched)
+    if action == "relaunch":
+        return _relaunch(args.gpus)
+    if action == "error":
+        print(f"bench.py: --gpus {args.gpus} but the launcher started {world} rank(s)", file=sys.stderr)
+        return 2
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -181,13 +181,19 @@ isr_status isr_plan_test_drop_window(isr_plan* plan, int32_t ipp);
  * file-scope device array of ISR_STATIC_SCRATCH_FLOATS floats (16 MiB) that every GPU
  * which loads this library keeps until the process exits; n_ranges * nfft must not
  * exceed it (ISR_ERR_INVALID_ARG otherwise).  Nothing is allocated: no cudaMalloc, no
- * cudaFree, no allocating library routine.  The first call on a device looks up the
- * array's device address (once per device, with that device current), so make that
- * first call before any stream capture.  Every call shares the array and its contents
- * stay from the last call: calls that overlap on the GPU (other host threads or other
- * streams) race and corrupt each other's results.  The call is stream-ordered on
- * desc->stream and returns after that stream has finished the work (so it can report
- * ISR_ERR_TIMEOUT from a bounded wait that ran out).
+ * cudaFree, no allocating library routine.  As in a plan, every FP32 partial sums at
+ * most 256 IPPs; the array holds C = min(65535, ISR_STATIC_SCRATCH_FLOATS / (n_ranges *
+ * nfft)) of them, so the IPPs run in blocks of at most C * 256 (one fused launch and one
+ * reduction each).  The first block's reduction writes `out`; each later block adds its
+ * sum (formed in double) to `out` with one FP32 rounding, so a call of B blocks carries at
+ * most B extra roundings of 2^-24 relative per bin (B = 1 whenever n_ipp <= C * 256).
+ * The first call on a device looks up the array's device address (once per device, with
+ * that device current), so make that first call before any stream capture.  Every call
+ * shares the array and its contents stay from the last call: calls that overlap on the
+ * GPU (other host threads or other streams) race and corrupt each other's results.  The
+ * call is synchronous: it enqueues its work on desc->stream and then waits for that
+ * stream (so it can report ISR_ERR_TIMEOUT from a bounded wait that ran out); a stream
+ * that is being captured does not allow that wait, so no call belongs inside a capture.
  */
 #define ISR_STATIC_SCRATCH_FLOATS (4 * 1024 * 1024)
 isr_status isr_integrate_static(const isr_plan_desc* desc, const int16_t* echo, const void* tx_code,

@@ -15,6 +15,10 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIB = os.path.join(LIBDIR, "libisr.so")
+# debug build: the kernels check every gate's staged window against its echo row
+# (-DISR_DEBUG; a failed check is reported as ISR_ERR_OUT_OF_RANGE, never a trap)
+OBJDIR_DEBUG = os.path.join(LIBDIR, "obj_debug")
+LIB_DEBUG = os.path.join(LIBDIR, "libisr_debug.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 UNITS = ["isr_api.cu", "isr_linefit.cu", "isr_peak.cu", "isr_estimator.cu", "isr_batch.cu", "isr_k_small.cu", "isr_k_mid.cu", "isr_k_8192.cu", "isr_k_16384.cu"]
@@ -34,12 +38,12 @@ def _stale(target, srcs):
     return any(os.path.getmtime(s) > t for s in srcs)
 
 
-def _compile(unit, verbose):
+def _compile(unit, verbose, debug=False):
     src = os.path.join(CSRC, unit)
-    obj = os.path.join(OBJDIR, unit.replace(".cu", ".o"))
+    obj = os.path.join(OBJDIR_DEBUG if debug else OBJDIR, unit.replace(".cu", ".o"))
     if not _stale(obj, [src] + _deps()):
         return obj, ""
-    cmd = ["nvcc", *ARCH, *FLAGS, "-c", src, "-o", obj + ".tmp"]
+    cmd = ["nvcc", *ARCH, *FLAGS, *(["-DISR_DEBUG=1"] if debug else []), "-c", src, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -49,25 +53,27 @@ def _compile(unit, verbose):
     return obj, r.stderr
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OBJDIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Build lib/libisr.so (or, with debug=True, lib/libisr_debug.so) and return its path."""
+    objdir, lib = (OBJDIR_DEBUG, LIB_DEBUG) if debug else (OBJDIR, LIB)
+    os.makedirs(objdir, exist_ok=True)
     if force:
-        for f in os.listdir(OBJDIR):
-            os.remove(os.path.join(OBJDIR, f))
+        for f in os.listdir(objdir):
+            os.remove(os.path.join(objdir, f))
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        results = list(ex.map(lambda u: _compile(u, verbose), UNITS))
+        results = list(ex.map(lambda u: _compile(u, verbose, debug), UNITS))
     objs = [o for o, _ in results]
     if verbose:
         for (_, log), u in zip(results, UNITS):
             if log:
                 print(f"--- {u}\n{log}")
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         subprocess.run(["nvcc", *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp], check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

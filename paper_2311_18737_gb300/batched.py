@@ -98,7 +98,7 @@ class Batch:
 
 
 def per_window(bufs: Buffers, outs=None, stream=None):
-    """The same windows through one plan each (isr_integrate + isr_spectra per window)."""
+    """The same windows through one plan each, created and destroyed per call."""
     stream = stream if stream is not None else torch.cuda.current_stream(bufs.dev)
     outs = outs if outs is not None else [torch.empty_like(o) for o in bufs.out]
     for w, e, c, o in zip(bufs.w, bufs.echo, bufs.code, outs):
@@ -107,6 +107,48 @@ def per_window(bufs: Buffers, outs=None, stream=None):
             p.integrate(e, c, w.n_ipp)
             p.spectra(o)
     return outs
+
+
+class PerWindowPlans:
+    """The same windows through one plan each, the plans created once and kept (what a caller
+    without batching does): a run integrates every window, then reads every window's spectra.
+    ``orders`` maps nfft to the radix order the plans use (the batch's autotuned orders)."""
+
+    def __init__(self, bufs: Buffers, orders=None, stream=None):
+        self.bufs = bufs
+        self.stream = stream if stream is not None else torch.cuda.current_stream(bufs.dev)
+        self.plans = []
+        for w in bufs.w:
+            p = isr.Plan(nfft=w.nfft, n_ranges=w.n_ranges, echo_stride=w.echo_stride, range_start=w.range_start,
+                         range_step=w.range_step, tx_type=isr.ISR_TX_PM1, device=bufs.dev.index, stream=self.stream)
+            if orders and orders.get(w.nfft):
+                isr.isr_plan_set_order(p.handle, orders[w.nfft])
+            self.plans.append(p)
+
+    def run(self, outs):
+        for p, w, e, c in zip(self.plans, self.bufs.w, self.bufs.echo, self.bufs.code):
+            p.integrate(e, c, w.n_ipp)
+        for p, o in zip(self.plans, outs):
+            p.spectra(o, isr.ISR_RESET_AFTER)
+
+    def close(self):
+        for p in self.plans:
+            p.close()
+        self.plans = []
+
+
+def _timed(fn, reps):
+    """(mean ms per call by CUDA events on the current stream, mean wall ms per call)."""
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev0.record()
+    for _ in range(reps):
+        fn()
+    ev1.record()
+    torch.cuda.synchronize()
+    wall = 1000 * (time.perf_counter() - t0) / reps
+    return ev0.elapsed_time(ev1) / reps, wall
 
 
 def bench(ipp_scale: float = 1.0, reps: int = 2, seed: int = 3):
@@ -120,30 +162,36 @@ def bench(ipp_scale: float = 1.0, reps: int = 2, seed: int = 3):
     b = Batch(bufs, flags=isr.ISR_BATCH_GRAPH | isr.ISR_BATCH_AUTOTUNE)
     create_s = time.time() - t0
     b.run()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for _ in range(reps):
+
+    def run_batched():
         b.run(wait=False)
-    ev1.record()
-    isr.isr_batch_wait(b.h)
-    batched_ms = ev0.elapsed_time(ev1) / reps
-    # per-window plans (created inside the timed loop, as a caller without batching would)
-    outs = per_window(bufs)
-    torch.cuda.synchronize()
-    ev0.record()
-    for _ in range(reps):
-        per_window(bufs, outs)
-    ev1.record()
-    torch.cuda.synchronize()
-    per_ms = ev0.elapsed_time(ev1) / reps
+        isr.isr_batch_wait(b.h)
+
+    batched_ms, batched_wall = _timed(run_batched, reps)
+    # fair baseline: per-window plans created once, before timing, with the batch's radix orders
+    binfo = b.info()
+    orders = dict(zip((2048, 4096, 8192, 16384), binfo["order"]))
+    pw = PerWindowPlans(bufs, orders)
+    outs = [torch.empty_like(o) for o in bufs.out]
+    pw.run(outs)
+    reused_ms, reused_wall = _timed(lambda: pw.run(outs), reps)
+    pw.close()
+    # context: plans created and destroyed inside every run
+    outs2 = per_window(bufs)
+    create_ms, create_wall = _timed(lambda: per_window(bufs, outs2), reps)
     diff = max(float(((o - r).abs() / r.abs().clamp_min(1e-30)).max()) for o, r in zip(bufs.out, outs))
     res = {"windows": [{"nfft": w.nfft, "gates": w.n_ranges, "ipps": w.n_ipp,
                         "channel": "down" if i % 2 else "up"} for i, w in enumerate(ws)],
-           "transforms": transforms, "batched_ms": batched_ms, "per_window_ms": per_ms,
+           "transforms": transforms,
+           "batched_ms": batched_ms, "batched_wall_ms": batched_wall,
+           "per_window_ms": reused_ms, "per_window_wall_ms": reused_wall,
+           "per_window_create_each_run_ms": create_ms, "per_window_create_each_run_wall_ms": create_wall,
            "batched_spectra_per_s": transforms / (batched_ms / 1e3),
-           "per_window_spectra_per_s": transforms / (per_ms / 1e3),
-           "speedup": per_ms / batched_ms, "max_rel_diff_batched_vs_per_window": diff,
-           "batch": b.info(), "generation_s": gen_s, "create_s": create_s, "reps": reps}
+           "per_window_spectra_per_s": transforms / (reused_ms / 1e3),
+           "speedup": reused_ms / batched_ms,
+           "speedup_vs_plans_created_each_run": create_ms / batched_ms,
+           "max_rel_diff_batched_vs_per_window": diff,
+           "batch": binfo, "generation_s": gen_s, "create_s": create_s, "reps": reps}
     b.close()
     return res
 

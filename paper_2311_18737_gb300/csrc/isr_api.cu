@@ -480,6 +480,8 @@ isr_status isr_spectra(isr_plan* p, float* out, int32_t flags, int64_t* n_ipp_ou
     if (status) {
         CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
         CUDA_TRY(cudaStreamSynchronize(p->stream));
+        if (status & 2)
+            return fail(ISR_ERR_OUT_OF_RANGE, "a kernel found a gate window outside its echo row (debug build check)");
         return fail(ISR_ERR_TIMEOUT, "a kernel timed out waiting for its staged echo window");
     }
     return ISR_OK;
@@ -566,12 +568,13 @@ std::mutex g_static_mu;
 float* g_static_scratch_ptr[kMaxDevices] = {};
 int* g_static_status_ptr[kMaxDevices] = {};
 
-// out[i] = (float) sum_c part[c][i], summed in double
+// out[i] = (float) sum_c part[c][i] (first block of IPPs) or (float)(out[i] + sum_c part[c][i])
+// (later blocks), summed in double: one FP32 rounding of the running sum per block
 __global__ void reduce_to_spectra_kernel(const float* __restrict__ part, int n_chunks, int64_t n,
-                                         float* __restrict__ out)
+                                         float* __restrict__ out, int accumulate)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0;
+        double s = accumulate ? (double)out[i] : 0.0;
         for (int c = 0; c < n_chunks; ++c) s += part[(int64_t)c * n + i];
         out[i] = (float)s;
     }
@@ -651,42 +654,54 @@ isr_status isr_integrate_static(const isr_plan_desc* desc, const int16_t* echo, 
     CUDA_TRY(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
     cudaStream_t stream = static_cast<cudaStream_t>(d.stream);
 
-    // chunks: FP32 sums of at most kDefaultChunk IPPs while the scratch allows, two waves of
-    // CTAs when the IPP count allows, never more chunks than fit in the scratch
+    // Chunks: FP32 sums of at most kDefaultChunk IPPs (the bound the per-bin tolerance rests
+    // on), at most c_cap of them in the scratch at once.  The IPPs run in blocks of at most
+    // c_cap * kDefaultChunk: one fused launch and one reduction per block, the reduction of
+    // every block after the first adding into `out`.  Within a block, two waves of CTAs when
+    // the IPP count allows.
     const int rg = (d.n_ranges + ke.gates - 1) / ke.gates;
     const int64_t c_cap = std::min<int64_t>(65535, ISR_STATIC_SCRATCH_FLOATS / RN);
-    int64_t c_min = (n_ipp + kDefaultChunk - 1) / kDefaultChunk;
-    int64_t c_fill = (2 * (int64_t)sm_count + rg - 1) / rg;
-    int64_t C = std::min(c_cap, std::max(c_min, std::min<int64_t>(c_fill, n_ipp)));
-    int64_t chunk = (n_ipp + C - 1) / C;
-    C = (n_ipp + chunk - 1) / chunk;
+    const int64_t block_cap = c_cap * kDefaultChunk;
+    const int64_t c_fill = (2 * (int64_t)sm_count + rg - 1) / rg;
 
     CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), stream));
-    isr::KArgs a;
-    a.echo = reinterpret_cast<const uint32_t*>(echo);
-    a.echo_stride = d.echo_stride;
-    a.tx = tx;
-    a.tx_stride = d.tx_stride;
-    a.partial = scratch;
-    a.status = status;
-    a.n_ranges = d.n_ranges;
-    a.range_start = d.range_start;
-    a.range_step = d.range_step;
-    a.code_len = d.code_len;
-    a.n_ipp = n_ipp;
-    a.chunk_len = (int)chunk;
-    a.wait_limit = kDefaultWaitLimit;
-    a.drop_ipp = -1;
-    void* args[] = {&a};
-    CUDA_TRY(cudaLaunchKernel(ke.fn, dim3((unsigned)rg, (unsigned)C), dim3((unsigned)ke.threads), args,
-                              (size_t)ke.smem, stream));
-    int threads = 256;
-    int64_t blocks = std::min<int64_t>((RN + threads - 1) / threads, (int64_t)sm_count * 8);
-    reduce_to_spectra_kernel<<<(unsigned)blocks, threads, 0, stream>>>(scratch, (int)C, RN, out);
-    CUDA_TRY(cudaGetLastError());
+    const int cb = chip_bytes(d.tx_type);
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((RN + threads - 1) / threads, (int64_t)sm_count * 8);
+    for (int64_t done = 0; done < n_ipp;) {
+        const int64_t n_l = std::min<int64_t>(n_ipp - done, block_cap);
+        const int64_t c_min = (n_l + kDefaultChunk - 1) / kDefaultChunk;
+        int64_t C = std::min(c_cap, std::max(c_min, std::min<int64_t>(c_fill, n_l)));
+        const int64_t chunk = (n_l + C - 1) / C;
+        C = (n_l + chunk - 1) / chunk;
+
+        isr::KArgs a;
+        a.echo = reinterpret_cast<const uint32_t*>(echo) + done * d.echo_stride;
+        a.echo_stride = d.echo_stride;
+        a.tx = static_cast<const char*>(tx) + (size_t)(done * d.tx_stride) * cb;
+        a.tx_stride = d.tx_stride;
+        a.partial = scratch;
+        a.status = status;
+        a.n_ranges = d.n_ranges;
+        a.range_start = d.range_start;
+        a.range_step = d.range_step;
+        a.code_len = d.code_len;
+        a.n_ipp = (int)n_l;
+        a.chunk_len = (int)chunk;
+        a.wait_limit = kDefaultWaitLimit;
+        a.drop_ipp = -1;
+        void* args[] = {&a};
+        CUDA_TRY(cudaLaunchKernel(ke.fn, dim3((unsigned)rg, (unsigned)C), dim3((unsigned)ke.threads), args,
+                                  (size_t)ke.smem, stream));
+        reduce_to_spectra_kernel<<<(unsigned)blocks, threads, 0, stream>>>(scratch, (int)C, RN, out, done > 0);
+        CUDA_TRY(cudaGetLastError());
+        done += n_l;
+    }
     int flag = 0;
     CUDA_TRY(cudaMemcpyAsync(&flag, status, sizeof(int), cudaMemcpyDeviceToHost, stream));
     CUDA_TRY(cudaStreamSynchronize(stream));
+    if (flag & 2)
+        return fail(ISR_ERR_OUT_OF_RANGE, "a kernel found a gate window outside its echo row (debug build check)");
     if (flag) return fail(ISR_ERR_TIMEOUT, "a kernel timed out waiting for its staged echo window");
     return ISR_OK;
 }

@@ -450,6 +450,8 @@ isr_status isr_batch_wait(isr_batch* b)
     if (e == cudaSuccess && status) e = cudaMemsetAsync(b->status, 0, sizeof(int), b->user_stream);
     if (prev >= 0) cudaSetDevice(prev);
     if (e != cudaSuccess) return fail(ISR_ERR_CUDA, "isr_batch_wait: %s", cudaGetErrorString(e));
+    if (status & 2)
+        return fail(ISR_ERR_OUT_OF_RANGE, "a batched unit found a gate window outside its echo row (debug build check)");
     if (status) return fail(ISR_ERR_TIMEOUT, "a batched unit timed out waiting for its staged window");
     return ISR_OK;
 }

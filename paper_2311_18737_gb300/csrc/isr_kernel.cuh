@@ -348,6 +348,30 @@ __device__ __forceinline__ void twiddle_tab3(float2* v, const float2* tab, int j
     }
 }
 
+// ---------------------------------------------------------------- debug-build window check
+// With -DISR_DEBUG every gate checks, before it stages anything, that its window copy lies
+// inside the echo row (s_r >= 0, s_r + code_len <= echo_stride, the 16-byte-rounded copy
+// [s_r - off, s_r - off + words) within the row) and fits the stage buffer.  A gate that
+// fails sets bit 1 of the status word and never issues a copy: its bounded waits then run
+// out and the unit ends through the timeout path, with no access outside any buffer.  The
+// release build checks nothing here (the host validates the geometry before every launch).
+template <class A>
+__device__ __forceinline__ bool debug_window_ok(const A& a, int64_t s_r, int off, uint32_t copy_bytes,
+                                                int stage_words, int t)
+{
+#ifdef ISR_DEBUG
+    const int64_t first = s_r - off, words = (int64_t)(copy_bytes / 4);
+    const bool ok = s_r >= 0 && a.code_len >= 1 && s_r + a.code_len <= a.echo_stride && first >= 0 &&
+                    (first & 3) == 0 && first + words <= a.echo_stride && off + a.code_len <= stage_words &&
+                    words <= stage_words;
+    if (!ok && t == 0) atomicOr(a.status, 2);
+    return ok;
+#else
+    (void)a, (void)s_r, (void)off, (void)copy_bytes, (void)stage_words, (void)t;
+    return true;
+#endif
+}
+
 // ---------------------------------------------------------------- the fused work unit
 // One unit = gates [gx G, gx G + G) of IPP chunk c of the launch `a`.  Each gate group g
 // owns mbarrier slot g (initialised by the caller); phase0 is the number of phases that
@@ -417,6 +441,7 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
     // window geometry: the copy starts at the 16-byte boundary at or below s_r
     const int off = (int)(s_r & 3);
     const uint32_t copy_bytes = (uint32_t)(((off + a.code_len + 3) & ~3) * 4);
+    const bool dbg_ok = debug_window_ok(a, s_r, off, copy_bytes, S::STAGE_WORDS, t);
     auto issue = [&](int p) {
         const uint32_t* src = a.echo + (int64_t)p * a.echo_stride + (s_r - off);
         if constexpr (P0 == P0_SIMT) {
@@ -467,7 +492,7 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
     }
     __syncthreads();
 
-    if (t == 0 && p_begin < p_end && p_begin != a.drop_ipp) issue(p_begin);
+    if (t == 0 && dbg_ok && p_begin < p_end && p_begin != a.drop_ipp) issue(p_begin);
 
     const char* txbase = reinterpret_cast<const char*>(a.tx);
     constexpr int CHIP = TXT == TX_CI16 ? 4 : TXT == TX_C32 ? 8 : 1;
@@ -530,7 +555,7 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
 
         // window fully consumed and first-pass outputs visible
         gsync();
-        if (t == 0 && p + 1 < p_end && p + 1 != a.drop_ipp) {
+        if (t == 0 && dbg_ok && p + 1 < p_end && p + 1 != a.drop_ipp) {
             fence_proxy_async();
             issue(p + 1);
         }
@@ -682,6 +707,7 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
     const uint32_t bar = smem_u32(&mbar[g]);
     const int off = (int)(s_r & 3);
     const uint32_t copy_bytes = (uint32_t)(((off + a.code_len + 3) & ~3) * 4);
+    const bool dbg_ok = debug_window_ok(a, s_r, off, copy_bytes, S::STAGE_WORDS, t);
     auto issue = [&](int p) {
         const uint32_t* src = a.echo + (int64_t)p * a.echo_stride + (s_r - off);
         bulk_load(smem_u32(stage), src, copy_bytes, bar);
@@ -704,7 +730,7 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
         tabc[i] = make_float2(cs, sn);
     }
     __syncthreads();
-    if (t == 0 && p_begin < p_end && p_begin != a.drop_ipp) issue(p_begin);
+    if (t == 0 && dbg_ok && p_begin < p_end && p_begin != a.drop_ipp) issue(p_begin);
 
     const char* txbase = reinterpret_cast<const char*>(a.tx);
     constexpr int CHIP = TXT == TX_CI16 ? 4 : TXT == TX_C32 ? 8 : 1;
@@ -777,7 +803,7 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
             });
         });
         __syncthreads();   // regions complete; the window is consumed
-        if (t == 0 && p + 1 < p_end && p + 1 != a.drop_ipp) {
+        if (t == 0 && dbg_ok && p + 1 < p_end && p + 1 != a.drop_ipp) {
             fence_proxy_async();
             issue(p + 1);
         }

@@ -167,6 +167,7 @@ __device__ __forceinline__ bool integrate_unit_p(const KArgs a, const int gx, co
     const uint32_t bar = smem_u32(&mbar[0]);
     const int off = (int)(s_r & 3);
     const uint32_t copy_bytes = (uint32_t)(((off + a.code_len + 3) & ~3) * 4);
+    const bool dbg_ok = debug_window_ok(a, s_r, off, copy_bytes, S::STAGE_WORDS, t);
     auto issue = [&](int p) {
         const uint32_t* src = a.echo + (int64_t)p * a.echo_stride + (s_r - off);
         bulk_load(smem_u32(stage), src, copy_bytes, bar);
@@ -186,7 +187,7 @@ __device__ __forceinline__ bool integrate_unit_p(const KArgs a, const int gx, co
         }
     }
     __syncthreads();
-    if (t == 0 && p_begin < p_end && p_begin != a.drop_ipp) issue(p_begin);
+    if (t == 0 && dbg_ok && p_begin < p_end && p_begin != a.drop_ipp) issue(p_begin);
 
     const int8_t* code = reinterpret_cast<const int8_t*>(a.tx);
     // chips of pass 0: bit (2 m + e) * 4 + k for position 2 (t + 512 m) + e + 4096 k
@@ -255,7 +256,7 @@ __device__ __forceinline__ bool integrate_unit_p(const KArgs a, const int gx, co
             }
         }
         __syncthreads();   // pass-0 outputs complete; the window is consumed
-        if (t == 0 && p + 1 < p_end && p + 1 != a.drop_ipp) {
+        if (t == 0 && dbg_ok && p + 1 < p_end && p + 1 != a.drop_ipp) {
             fence_proxy_async();
             issue(p + 1);
         }
@@ -407,6 +408,7 @@ __device__ __forceinline__ bool integrate_unit_q(const KArgs a, const int gx, co
     const uint32_t bar = smem_u32(&mbar[0]);
     const int off = (int)(s_r & 3);
     const uint32_t copy_bytes = (uint32_t)(((off + a.code_len + 3) & ~3) * 4);
+    const bool dbg_ok = debug_window_ok(a, s_r, off, copy_bytes, S::STAGE_WORDS, t);
     auto issue = [&](int p) {
         const uint32_t* src = a.echo + (int64_t)p * a.echo_stride + (s_r - off);
         bulk_load(smem_u32(stage), src, copy_bytes, bar);
@@ -431,7 +433,7 @@ __device__ __forceinline__ bool integrate_unit_q(const KArgs a, const int gx, co
         }
     }
     __syncthreads();
-    if (t == 0 && p_begin < p_end && p_begin != a.drop_ipp) issue(p_begin);
+    if (t == 0 && dbg_ok && p_begin < p_end && p_begin != a.drop_ipp) issue(p_begin);
 
     const int8_t* code = reinterpret_cast<const int8_t*>(a.tx);
     // chips of pass 0: bit b * 16 + k for position t + 512 b + 1024 k (radix order 1's layout)
@@ -476,7 +478,7 @@ __device__ __forceinline__ bool integrate_unit_q(const KArgs a, const int gx, co
 #pragma unroll
         for (int q = 0; q < 16; ++q) x1[qslot(16 * t) + q] = make_float4(v[q].re.x, v[q].re.y, v[q].im.x, v[q].im.y);
         __syncthreads();   // pass-0 outputs complete; the window is consumed
-        if (t == 0 && p + 1 < p_end && p + 1 != a.drop_ipp) {
+        if (t == 0 && dbg_ok && p + 1 < p_end && p + 1 != a.drop_ipp) {
             fence_proxy_async();
             issue(p + 1);
         }

@@ -11,7 +11,9 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "lib", "libisr.so")
+# ISR_LIBRARY selects another build of the library (for example lib/libisr_debug.so, whose
+# kernels check every staged window against its echo row)
+LIB_PATH = os.environ.get("ISR_LIBRARY") or os.path.join(_HERE, "lib", "libisr.so")
 
 ISR_OK = 0
 ISR_ERR_INVALID_ARG = 1

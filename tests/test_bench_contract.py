@@ -58,9 +58,10 @@ def test_our_arm_line():
 
 
 @pytest.mark.gpu
-def test_torchrun_launch_one_rank():
+@pytest.mark.parametrize("scaling", ["weak", "strong"])
+def test_torchrun_launch_one_rank(scaling):
     # the launch the harness uses for N GPUs, here with one rank: NCCL process group, barriers
-    # and the max over ranks all run
+    # and the max over ranks all run (strong: the gate-block partition, echo sub-span and gather)
     import socket
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
@@ -68,10 +69,18 @@ def test_torchrun_launch_one_rank():
     r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "1",
                         "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
                         "--gpus", "1", "--steps", "2", "--warmup", "3", "--n-ranges", "32", "--n-ipp", "64",
-                        "--e2e-steps", "1", "--no-cpu-baseline", "--no-peak"],
+                        "--e2e-steps", "1", "--no-cpu-baseline", "--no-peak", "--scaling", scaling],
                        cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1, r.stdout[-2000:]
     d = json.loads(lines[0])
-    assert d["n_gpus"] == 1 and d["value"] > 0 and d["e2e"]["value"] > 0
+    assert d["n_gpus"] == 1 and d["value"] > 0 and d["e2e"]["value"] > 0 and d["scaling"] == scaling
+
+
+def test_gpus_mismatch_under_a_launcher_exits_2():
+    # a launcher that started one rank while --gpus asks for two: refuse, do not measure one GPU
+    env = dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--impl", "reference"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=120, env=env)
+    assert r.returncode == 2 and "--gpus 2" in r.stderr

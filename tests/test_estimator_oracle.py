@@ -113,3 +113,55 @@ def test_storage_rounding_is_applied_where_the_bf16_variant_stores():
     x_off = x + 2.0 ** -12                          # off the BF16 grid near 1, 2, 3
     z_off, _, _ = est.forward(theta, x_off, est.round_bf16)
     assert not np.array_equal(z_off, est.forward(theta, x_off)[0])
+
+
+def test_presence_head_hand_worked():
+    """The presence head at non-zero weights, worked out by hand.
+
+    Channel 0 carries relu(x) through the four layers (centre tap 1), channel 1 carries the
+    constant 2 (bias 2 in layer 1, centre tap 1 after); every other channel is zero.  With
+    x = [0, 1, 3, -2, 0, 0, 0, 0]: h4[0] = [0, 1, 3, 0, 0, 0, 0, 0], h4[1] = 2 everywhere, so
+    the pooled vector is max = (3, 2, 0...), mean = (0.5, 2, 0...).  Head rows:
+      u0 = relu(1*3 + 2*0.5 - 1)          = 3
+      u1 = relu(-1*2 + 0.5*2 + 0.5)       = relu(-0.5) = 0
+      u2 = relu(4*0.5 - 0.25*2 + 0)       = 1.5
+      q  = 0.5*3 + 10*0 - 2*1.5 + 0.25    = -1.25,   presence = 1 / (1 + e^1.25) = 0.2227001388...
+    Location logits z = 1*h4[0] + 0.5*h4[1] - 1 = [0, 1, 3, 0, 0, 0, 0, 0].
+    Gradients of the loss at label 1 (batch of one): dq = presence - 1; d bb = dq,
+    d wb = dq u = dq (3, 0, 1.5), d ba = dq wb [u > 0] = dq (0.5, 0, -2),
+    d Wa[0][0] = dq 0.5 * 3, d Wa[0][32] = dq 0.5 * 0.5, d Wa[1][*] = 0, d Wa[2][32] = dq (-2) 0.5."""
+    d = est.unpack(np.zeros(est.N_PARAMS))
+    for l in range(1, 5):
+        W = np.zeros_like(d[f"W{l}"])
+        W[0, 0, est.HALF] = 1.0
+        if l > 1:
+            W[1, 1, est.HALF] = 1.0
+        d[f"W{l}"] = W
+    d["b1"][1] = 2.0
+    d["w5"][0], d["w5"][1], d["b5"][0] = 1.0, 0.5, -1.0
+    d["Wa"][0, 0], d["Wa"][0, 32], d["ba"][0] = 1.0, 2.0, -1.0
+    d["Wa"][1, 1], d["Wa"][1, 33], d["ba"][1] = -1.0, 0.5, 0.5
+    d["Wa"][2, 32], d["Wa"][2, 33] = 4.0, -0.25
+    d["wb"][0], d["wb"][1], d["wb"][2], d["bb"][0] = 0.5, 10.0, -2.0, 0.25
+    theta = est.pack(d)
+    x = np.array([[0.0, 1.0, 3.0, -2.0, 0.0, 0.0, 0.0, 0.0]])
+
+    z, q, cache = est.forward(theta, x)
+    np.testing.assert_array_equal(cache["pooled"][0, :3], [3.0, 2.0, 0.0])
+    np.testing.assert_array_equal(cache["pooled"][0, 32:35], [0.5, 2.0, 0.0])
+    np.testing.assert_array_equal(cache["u"][0, :3], [3.0, 0.0, 1.5])
+    assert q[0] == -1.25
+    np.testing.assert_array_equal(z[0], [0.0, 1.0, 3.0, 0.0, 0.0, 0.0, 0.0, 0.0])
+    pos, pres = est.predict(theta, x)
+    assert abs(pres[0] - 0.22270013882530884) < 1e-15
+
+    _, g = est.loss_and_grad(theta, x, np.array([2.0]), np.array([1.0]))
+    gd = est.unpack(g)
+    dq = 0.22270013882530884 - 1.0
+    assert abs(gd["bb"][0] - dq) < 1e-14
+    np.testing.assert_allclose(gd["wb"][:3], [3 * dq, 0.0, 1.5 * dq], rtol=0, atol=1e-14)
+    assert np.all(gd["wb"][3:] == 0)
+    np.testing.assert_allclose(gd["ba"][:3], [0.5 * dq, 0.0, -2.0 * dq], rtol=0, atol=1e-14)
+    assert abs(gd["Wa"][0, 0] - 1.5 * dq) < 1e-14 and abs(gd["Wa"][0, 32] - 0.25 * dq) < 1e-14
+    assert np.all(gd["Wa"][1] == 0)
+    assert abs(gd["Wa"][2, 32] - (-1.0 * dq)) < 1e-14 and abs(gd["Wa"][2, 33] - (-4.0 * dq)) < 1e-14

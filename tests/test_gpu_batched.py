@@ -70,3 +70,16 @@ def test_bad_window_rejected(bufs):
     with pytest.raises(isr.IsrError) as ei:
         isr.isr_batch_create(ws, 0, 0, torch.cuda.current_stream())
     assert ei.value.status == isr.ISR_ERR_UNSUPPORTED
+
+
+def test_reused_per_window_plans_match_fresh_plans(bufs, reference):
+    # the batched comparison's baseline: plans created once and reused over two runs
+    pw = batched.PerWindowPlans(bufs, orders={2048: 1, 4096: 0, 8192: 2, 16384: 1})
+    try:
+        for _ in range(2):
+            outs = [torch.empty_like(o) for o in bufs.out]
+            pw.run(outs)
+            for i, (o, r) in enumerate(zip(outs, reference)):
+                assert_parity(o.cpu().numpy().astype(np.float64), r, rtol=RTOL, what=f"reused plan, window {i}")
+    finally:
+        pw.close()
