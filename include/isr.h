@@ -140,28 +140,39 @@ isr_status isr_plan_set_profiling(isr_plan* plan, int32_t enable);
  * and return; the next isr_spectra reports ISR_ERR_TIMEOUT.  polls must be > 0. */
 isr_status isr_plan_set_wait_limit(isr_plan* plan, uint32_t polls);
 
-/* Radix order (0..5) of the kernel used for binary-phase codes with code_len == nfft, for
+/* Radix order (0..8) of the kernel used for binary-phase codes with code_len == nfft, for
  * nfft >= 2048 (smaller sizes have one order): 0..2 are three-pass Stockham orders, 3 is a
  * radix-(nfft/1024) decimation-in-frequency pass followed by one 1024-point transform per
  * warp; 4 and 5 (nfft 16384 only) use paired FP32 instructions (two operations each):
  * 4 the passes [4, 16, 16, 16] with each thread transforming two butterflies at once,
  * 5 the passes [16, 32, 32] of order 1 with two butterflies per thread in the first pass
- * and each radix-32 butterfly split into two paired 16-point halves.  Every order gives
+ * and each radix-32 butterfly split into two paired 16-point halves; 6, 7 and 8 (nfft
+ * 16384 only) are orders 0, 1 and 2 with every thread's inter-pass twiddles computed once
+ * per CTA into tensor memory (all 512 columns of the SM's TMEM, freed when the CTA ends)
+ * instead of being formed from tables and recurrences in every IPP.  Every order gives
  * the same spectra up to FP32 rounding; they differ in speed, so a caller (or the
  * binding's autotuner) may time them and keep the fastest.  Default 0. */
 isr_status isr_plan_set_order(isr_plan* plan, int32_t order);
 
 /* Engine of the first FFT pass.  ISR_PREC_FP32 (default): SIMT FP32 everywhere.  The
- * ISR_PREC_TC_* modes (nfft 16384, ISR_TX_PM1, code_len == nfft) compute the first pass
+ * tensor-core modes (nfft 16384, ISR_TX_PM1, code_len == nfft) compute the first pass
  * (radix 16 over the window, then radix 32, 32 on the SIMT pipe) as a DFT-matrix GEMM on
  * the tensor cores with FP32 accumulation: *_SPLIT modes use hi + lo operand splits
  * (A_hi B_hi + A_hi B_lo + A_lo B_hi) in BF16 or FP16, the others a single BF16 or FP16
- * product.  Accumulation over IPPs stays FP32 per chunk and FP64 across chunks. */
+ * product.  ISR_PREC_TC_* issue the warp-level mma.sync instruction with register
+ * fragments; ISR_PREC_TC05_* issue tcgen05.mma from one thread with both operands in shared
+ * memory (decoded samples split once into K-major operand tiles) and the FP32 accumulator
+ * in tensor memory (256 columns per CTA, freed when the CTA ends).  Accumulation over IPPs
+ * stays FP32 per chunk and FP64 across chunks. */
 #define ISR_PREC_FP32 0
 #define ISR_PREC_TC_BF16_SPLIT 1
 #define ISR_PREC_TC_FP16_SPLIT 2
 #define ISR_PREC_TC_BF16 3
 #define ISR_PREC_TC_FP16 4
+#define ISR_PREC_TC05_BF16_SPLIT 5
+#define ISR_PREC_TC05_FP16_SPLIT 6
+#define ISR_PREC_TC05_BF16 7
+#define ISR_PREC_TC05_FP16 8
 isr_status isr_plan_set_precision(isr_plan* plan, int32_t precision);
 
 /* Test hook: the kernels of the following isr_integrate calls never stage the window of

@@ -387,7 +387,7 @@ isr_status isr_plan_create(isr_plan** out, const isr_plan_desc* desc)
     if (p->ke.smem > smem_optin)
         return bail(fail(ISR_ERR_UNSUPPORTED, "kernel needs %d B shared memory, device allows %d", p->ke.smem, smem_optin));
     e = cudaFuncSetAttribute(p->ke.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->ke.smem);
-    for (int o = 0; o < 6 && e == cudaSuccess; ++o)
+    for (int o = 0; o < isr::kNumOrders && e == cudaSuccess; ++o)
         e = cudaFuncSetAttribute(p->ke.fn_order[o], cudaFuncAttributeMaxDynamicSharedMemorySize, p->ke.smem_order[o]);
     if (e != cudaSuccess) return bail(fail(ISR_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
 
@@ -521,17 +521,18 @@ isr_status isr_plan_set_wait_limit(isr_plan* p, uint32_t polls)
 
 isr_status isr_plan_set_order(isr_plan* p, int32_t order)
 {
-    if (!p || order < 0 || order > 5) return fail(ISR_ERR_INVALID_ARG, "plan is NULL or order not in 0..5");
+    if (!p || order < 0 || order >= isr::kNumOrders)
+        return fail(ISR_ERR_INVALID_ARG, "plan is NULL or order not in 0..%d", isr::kNumOrders - 1);
     if (p->d.nfft < 2048 && order != 0) return fail(ISR_ERR_UNSUPPORTED, "radix orders exist for nfft >= 2048 only");
     if (order >= 4 && (p->d.nfft != 16384 || p->d.tx_type != ISR_TX_PM1))
-        return fail(ISR_ERR_UNSUPPORTED, "radix orders 4 and 5 (paired) exist for nfft 16384 with ISR_TX_PM1 only");
+        return fail(ISR_ERR_UNSUPPORTED, "radix orders 4 to 8 exist for nfft 16384 with ISR_TX_PM1 only");
     p->order = order;
     return ISR_OK;
 }
 
 isr_status isr_plan_set_precision(isr_plan* p, int32_t precision)
 {
-    if (!p || precision < ISR_PREC_FP32 || precision > ISR_PREC_TC_FP16)
+    if (!p || precision < ISR_PREC_FP32 || precision > ISR_PREC_TC05_FP16)
         return fail(ISR_ERR_INVALID_ARG, "plan is NULL or unknown precision %d", precision);
     if (precision != ISR_PREC_FP32) {
         if (p->d.nfft != 16384 || p->d.tx_type != ISR_TX_PM1 || p->d.code_len != p->d.nfft || !p->ke.fn_tc[precision])

@@ -21,6 +21,8 @@
 
 #include "isr_fft.cuh"
 #include "isr_tc.cuh"
+#include "isr_tc05.cuh"
+#include "isr_tmem.cuh"
 
 namespace isr {
 
@@ -46,7 +48,10 @@ __host__ __device__ constexpr int radix_of(int log2n, int order, int p)
 }
 constexpr int kOrders = 4;   // 0..2 Stockham orders, 3 the warp-local schedule
 
-template <int LOG2N, int ORDER = 0>
+// TMT: the inter-pass twiddles of passes 1 and 2 are precomputed per thread into tensor
+// memory once per CTA (three-pass sizes with a first radix >= 16) instead of being formed
+// from tables and recurrences in every IPP.
+template <int LOG2N, int ORDER = 0, bool TMT = false>
 struct Sched {
     static constexpr int N = 1 << LOG2N;
     static constexpr int E = N < 32 ? N : 32;   // points per thread
@@ -69,10 +74,14 @@ struct Sched {
     // radix 16 and 32 keep only (w, w^2), (w^3, w^4), (w^8, w^16) per j mod Ns (6 entries) and
     // form the other powers with one product each; smaller radices keep every power
     __host__ __device__ static constexpr int tabw(int p) { return radix(p) >= 16 ? 6 : radix(p); }
-    static constexpr int TAB1 = (NP > 1 && tab(1)) ? ns(1) * tabw(1) : 0;
-    static constexpr int TAB2 = (NP > 2 && tab(2)) ? ns(2) * tabw(2) : 0;
-    static constexpr int SLOTS1 = (NP > 1 && !tab(1)) ? E / R1 : 0;           // per-thread bases
-    static constexpr int SLOTS2 = (NP > 2 && !tab(2)) ? E / R2 : 0;
+    static constexpr int TAB1 = (!TMT && NP > 1 && tab(1)) ? ns(1) * tabw(1) : 0;
+    static constexpr int TAB2 = (!TMT && NP > 2 && tab(2)) ? ns(2) * tabw(2) : 0;
+    static constexpr int SLOTS1 = (!TMT && NP > 1 && !tab(1)) ? E / R1 : 0;           // per-thread bases
+    static constexpr int SLOTS2 = (!TMT && NP > 2 && !tab(2)) ? E / R2 : 0;
+    // TMEM twiddles: per thread and pass, (E / R)(R - 1) <= 31 complex values as [b][k - 1] in
+    // 64 columns of the thread's lane; the warps of one lane quarter take 128 columns each
+    static_assert(!TMT || (NP == 3 && R0 >= 16 && kThreads == 512), "TMEM twiddles: three-pass sizes, first radix >= 16");
+    static constexpr int TM_COLS = 512;
     static constexpr int NSLOT = SLOTS1 + SLOTS2;
     // shared-memory exchange buffer: one pad element per PADP keeps every access pattern
     // of the passes free of bank conflicts (stride R0 + 1 for the first pass' writes)
@@ -89,7 +98,8 @@ struct Sched {
     static constexpr int OFF_MBAR = 0;
     // at least 8 mbarrier slots: the batched launch keeps slots 0..7 alive across shapes
     static constexpr int OFF_TW = 16 * ((8 * (G < 8 ? 8 : G) + 15) / 16);
-    static constexpr int OFF_TAB = OFF_TW + 16 * ((8 * NSLOT * T + 15) / 16);
+    static constexpr int OFF_TMEMADDR = OFF_TW;   // the CTA's TMEM base address (TMT)
+    static constexpr int OFF_TAB = OFF_TW + 16 * ((8 * NSLOT * T + 15) / 16) + (TMT ? 16 : 0);
     static constexpr int OFF_STAGE = OFF_TAB + 16 * ((8 * (TAB1 + TAB2) + 15) / 16);
     static constexpr int OFF_XCH = OFF_STAGE + 4 * STAGE_WORDS * G;
     static constexpr int SMEM = OFF_XCH + 8 * NPAD * G;
@@ -348,6 +358,29 @@ __device__ __forceinline__ void twiddle_tab3(float2* v, const float2* tab, int j
     }
 }
 
+// apply w^k (k = 1..R-1) to butterfly B of a pass from this thread's TMEM twiddles (complex
+// index e = B (R - 1) + k - 1, eight per 16-column load)
+template <int R, int B>
+__device__ __forceinline__ void twiddle_tmem(float2* u, uint32_t addr)
+{
+    constexpr int e0 = B * (R - 1), e1 = e0 + R - 1;
+    static_for<4>([&](auto Cc) {
+        constexpr int c = decltype(Cc)::value;
+        if constexpr (8 * c < e1 && 8 * c + 8 > e0) {
+            uint32_t r[16];
+            tmem_ld16(addr + 16 * c, r);
+            tmem_wait_ld(r);
+            static_for<8>([&](auto Ec) {
+                constexpr int i = decltype(Ec)::value, e = 8 * c + i;
+                if constexpr (e >= e0 && e < e1) {
+                    constexpr int k = e - e0 + 1;
+                    u[k] = cmul(u[k], make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1])));
+                }
+            });
+        }
+    });
+}
+
 // ---------------------------------------------------------------- debug-build window check
 // With -DISR_DEBUG every gate checks, before it stages anything, that its window copy lies
 // inside the echo row (s_r >= 0, s_r + code_len <= echo_stride, the 16-byte-rounded copy
@@ -383,11 +416,14 @@ __device__ __forceinline__ bool debug_window_ok(const A& a, int64_t s_r, int off
 // order 1, binary-phase, full-length codes only) a split-precision tensor-core GEMM.
 // A is how the arguments arrive: by value from a kernel parameter, or (persistent kernels) as a
 // reference to a shared-memory copy, read where needed rather than held in registers.
-template <int LOG2N, int TXT, int ORDER = 0, bool FULL = false, int P0 = P0_SIMT, class A = const KArgs>
+// TMT: twiddles of passes 1 and 2 from tensor memory at tmem (the CTA's allocation of
+// Sched::TM_COLS columns); setup writes them.
+template <int LOG2N, int TXT, int ORDER = 0, bool FULL = false, int P0 = P0_SIMT, class A = const KArgs,
+          bool TMT = false>
 __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, unsigned char* smem,
-                                               const uint32_t phase0, const bool setup)
+                                               const uint32_t phase0, const bool setup, const uint32_t tmem = 0)
 {
-    using S = Sched<LOG2N, ORDER>;
+    using S = Sched<LOG2N, ORDER, TMT>;
     constexpr int N = S::N, E = S::E, T = S::T, G = S::G, NP = S::NP;
     constexpr int R0 = S::R0;
     constexpr int RL = S::radix(NP - 1);  // radix of the last pass
@@ -397,7 +433,8 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
     constexpr bool CTA_SYNC = T > 32;
     static_assert(P0 == P0_SIMT || (LOG2N == 14 && ORDER == 1 && TXT == TX_PM1 && FULL),
                   "the tensor-core first pass exists for nfft 16384, radix order 1, full binary-phase codes");
-    uint4* afrag = reinterpret_cast<uint4*>(smem + S::SMEM);   // tensor-core A fragments
+    uint4* afrag = reinterpret_cast<uint4*>(smem + S::SMEM);   // tensor-core A fragments (mma.sync)
+    unsigned char* ftile = smem + S::SMEM;                      // DFT operator tiles (tcgen05)
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
     float2* twb = reinterpret_cast<float2*>(smem + S::OFF_TW);
     float2* tab = reinterpret_cast<float2*>(smem + S::OFF_TAB);
@@ -406,6 +443,7 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
     const int g = tid / T;
     const int t = tid - g * T;
     const int r = gx * G + g;
+    const uint32_t mma_bar = smem_u32(&mbar[G]); // tcgen05 first pass: the MMAs of this IPP completed
     auto gsync = [&]() {
         if constexpr (!CTA_SYNC) __syncwarp();
         else if constexpr (G == 1) __syncthreads();
@@ -444,7 +482,7 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
     const bool dbg_ok = debug_window_ok(a, s_r, off, copy_bytes, S::STAGE_WORDS, t);
     auto issue = [&](int p) {
         const uint32_t* src = a.echo + (int64_t)p * a.echo_stride + (s_r - off);
-        if constexpr (P0 == P0_SIMT) {
+        if constexpr (!p0_is_mmasync(P0)) {
             bulk_load(smem_u32(stage), src, copy_bytes, bar);
         } else {
             // 16 rows of 1024 samples (+4 words of alignment slack, inside the window's row),
@@ -474,8 +512,37 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
         sincospif(-2.f * (float)(j % ns) / (float)(ns * R), &sn, &cs);
         twb[i] = make_float2(cs, sn);
     }
-    if constexpr (P0 != P0_SIMT) {
+    if constexpr (p0_is_mmasync(P0)) {
         if (setup) tc_setup_afrags<P0>(afrag);
+    } else if constexpr (p0_is_tc05(P0)) {
+        if (setup) tc05_setup_f<P0>(ftile);
+    }
+    // this thread's TMEM twiddles: lane quarter of the warp, 128 columns per warp of the quarter
+    const uint32_t tw_tm = TMT ? tmem_warp_lane_base(tmem) + 128u * (uint32_t)(tid >> 7) : 0u;
+    if constexpr (TMT) {
+        if (setup) {
+            static_for<2>([&](auto Pc) {
+                constexpr int pass = decltype(Pc)::value + 1;
+                constexpr int R = S::radix(pass), NS = S::ns(pass), NB = E / R;
+                static_for<4>([&](auto Cc) {
+                    constexpr int cc = decltype(Cc)::value;
+                    uint32_t rr[16];
+                    static_for<8>([&](auto Ec) {
+                        constexpr int i = decltype(Ec)::value, e = 8 * cc + i;
+                        constexpr int b = e / (R - 1), k = e % (R - 1) + 1;
+                        float sn = 0.f, cs = 0.f;
+                        if constexpr (b < NB) {
+                            const int jm = (t + T * b) % NS;   // exact dyadic argument
+                            sincospif(-2.f * (float)((jm * k) % (NS * R)) / (float)(NS * R), &sn, &cs);
+                        }
+                        rr[2 * i] = __float_as_uint(cs);
+                        rr[2 * i + 1] = __float_as_uint(sn);
+                    });
+                    tmem_st16(tw_tm + 64u * (pass - 1) + 16u * cc, rr);
+                });
+            });
+            tmem_wait_st();
+        }
     }
     // twiddle tables of the small passes, w^k = exp(-2 pi i jm k / (Ns R)): float4 [p][jm] =
     // (w^{2p+1}, w^{2p+2}) for radix <= 8; for radix 16 and 32 the three pairs (w, w^2),
@@ -497,7 +564,7 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
     const char* txbase = reinterpret_cast<const char*>(a.tx);
     constexpr int CHIP = TXT == TX_CI16 ? 4 : TXT == TX_C32 ? 8 : 1;
     uint32_t signs = 0;
-    if constexpr (P0 != P0_SIMT) {
+    if constexpr (p0_is_mmasync(P0)) {
         if (a.tx_stride == 0) signs = tc_load_signs(reinterpret_cast<const int8_t*>(txbase));
     } else if constexpr (TXT == TX_PM1) {
         if (a.tx_stride == 0) signs = load_signs<LOG2N, ORDER>(reinterpret_cast<const int8_t*>(txbase), t, a.code_len);
@@ -511,24 +578,37 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
     bool timed_out = false;
     int it = 0;
     for (int p = p_begin; p < p_end; ++p, ++it) {
-        const bool ok = mbar_wait(bar, (phase0 + (uint32_t)it) & 1u, a.wait_limit);
+        bool ok = mbar_wait(bar, (phase0 + (uint32_t)it) & 1u, a.wait_limit);
         // every thread of the gate agrees before anyone leaves; this barrier also orders the
         // previous IPP's last-pass reads of xch before this IPP's first-pass writes
-        const bool any_fail = gsync_or(!ok);
-        if (any_fail) {
-            timed_out = true;
-            break;
+        {
+            const bool any_fail = gsync_or(!ok);
+            if (any_fail) {
+                timed_out = true;
+                break;
+            }
         }
         const char* txrow = txbase + (size_t)p * (size_t)a.tx_stride * CHIP;
-        if constexpr (P0 != P0_SIMT) {
+        if constexpr (p0_is_mmasync(P0)) {
             if (a.tx_stride != 0) signs = tc_load_signs(reinterpret_cast<const int8_t*>(txrow));
         } else if constexpr (TXT == TX_PM1) {
             if (a.tx_stride != 0) signs = load_signs<LOG2N, ORDER>(reinterpret_cast<const int8_t*>(txrow), t, a.code_len);
         }
 
         // ---- pass 0: decode from the staged window, radix-R0 DFT
-        if constexpr (P0 != P0_SIMT) tc_pass0<P0, S::PADP>(stage, off, signs, afrag, xch);
-        else static_for<E / R0>([&](auto Bc) {
+        if constexpr (p0_is_mmasync(P0)) {
+            tc_pass0<P0, S::PADP>(stage, off, signs, afrag, xch);
+        } else if constexpr (p0_is_tc05(P0)) {
+            // operand rows into the (free) exchange buffer, one thread issues the GEMM, every
+            // warp stores its rows of the result in Stockham order
+            tc05_build_operands<P0>(stage, off, signs, reinterpret_cast<unsigned char*>(xch));
+            gsync();
+            if (tid == 0) tc05_issue<P0>(smem_u32(xch), smem_u32(ftile), tmem, mma_bar);
+            ok = mbar_wait(mma_bar, (uint32_t)it & 1u, a.wait_limit) && ok;
+            tmem_fence_after_sync();
+            tc05_store_outputs<S::PADP>(tmem, xch);
+            tmem_fence_before_sync();
+        } else static_for<E / R0>([&](auto Bc) {
             constexpr int b = decltype(Bc)::value;
             const int j = t + T * b;
             float2* u = v + b * R0;
@@ -553,8 +633,16 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
             }
         });
 
-        // window fully consumed and first-pass outputs visible
-        gsync();
+        // window fully consumed and first-pass outputs visible (tcgen05 first pass: also the
+        // vote on its bounded wait for the GEMM)
+        if constexpr (p0_is_tc05(P0)) {
+            if (gsync_or(!ok)) {
+                timed_out = true;
+                break;
+            }
+        } else {
+            gsync();
+        }
         if (t == 0 && dbg_ok && p + 1 < p_end && p + 1 != a.drop_ipp) {
             fence_proxy_async();
             issue(p + 1);
@@ -572,7 +660,8 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
                 const int j = t + T * b;
                 float2* u = v + b * R;
                 load_strided<N / R, R, S::PADP>(u, xch, j);
-                if constexpr (S::tab(1) && R >= 16) twiddle_tab3<R, NS>(u, tab, j % NS);
+                if constexpr (TMT) twiddle_tmem<R, b>(u, tw_tm);
+                else if constexpr (S::tab(1) && R >= 16) twiddle_tab3<R, NS>(u, tab, j % NS);
                 else if constexpr (S::tab(1)) twiddle_tab<R, NS>(u, tab, j % NS);
                 else twiddle<R>(u, twb[b * T + t]);
                 dft<R, LOG2N >= 10>(u);
@@ -619,7 +708,8 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
                 } else {
                     load_strided<N / R, R, S::PADP>(u, xch, j);
                 }
-                if constexpr (S::tab(PL) && R >= 16) twiddle_tab3<R, S::ns(PL)>(u, tab + TAB0, j % S::ns(PL));
+                if constexpr (TMT) twiddle_tmem<R, b>(u, tw_tm + 64u);
+                else if constexpr (S::tab(PL) && R >= 16) twiddle_tab3<R, S::ns(PL)>(u, tab + TAB0, j % S::ns(PL));
                 else if constexpr (S::tab(PL)) twiddle_tab<R, S::ns(PL)>(u, tab + TAB0, j % S::ns(PL));
                 else twiddle<R>(u, twb[(SLOT0 + b) * T + t]);
                 dft<R, LOG2N >= 10>(u);
@@ -857,6 +947,57 @@ __global__ void __launch_bounds__(kThreads, 1) integrate_kernel_wl(KArgs a)
     if (threadIdx.x < S::G) mbar_init(smem_u32(&mbar[threadIdx.x]), 1);
     fence_barrier_init();
     integrate_unit_wl<LOG2N, TXT, FULL>(a, blockIdx.x, blockIdx.y, smem, 0u, true);
+}
+
+// One-shot launch with the inter-pass twiddles in tensor memory: warp 0 allocates all 512
+// columns (one CTA per SM: the shared memory admits no second one), every thread writes its
+// twiddles once, and warp 0 frees the columns after the unit, timed out or not.
+template <int LOG2N, int TXT, bool FULL, int ORDER>
+__global__ void __launch_bounds__(kThreads, 1) integrate_kernel_tm(KArgs a)
+{
+    using S = Sched<LOG2N, ORDER, true>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::OFF_TMEMADDR);
+    if (threadIdx.x < S::G) mbar_init(smem_u32(&mbar[threadIdx.x]), 1);
+    if (threadIdx.x < 32) tmem_alloc(smem_u32(tslot), S::TM_COLS);
+    fence_barrier_init();
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    const uint32_t tbase = *tslot;
+    integrate_unit<LOG2N, TXT, ORDER, FULL, P0_SIMT, const KArgs, true>(a, blockIdx.x, blockIdx.y, smem, 0u, true,
+                                                                         tbase);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (threadIdx.x < 32) tmem_dealloc(tbase, S::TM_COLS);
+}
+
+// One-shot launch with the first pass on tcgen05 (MODE one of P0_TC05_*): warp 0 allocates
+// the accumulator columns of the GEMM, mbarrier slot 1 tracks the GEMM of each IPP.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) integrate_kernel_tc05(KArgs a)
+{
+    using S = Sched<14, 1>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::OFF_MBAR + 8 * 7);   // slot 7 holds the address
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&mbar[0]), 1);   // staged window
+        mbar_init(smem_u32(&mbar[1]), 1);   // GEMM committed
+    }
+    if (threadIdx.x < 32) tmem_alloc(smem_u32(tslot), kTc05Cols);
+    fence_barrier_init();
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    const uint32_t tbase = *tslot;
+    integrate_unit<14, TX_PM1, 1, true, MODE>(a, blockIdx.x, blockIdx.y, smem, 0u, true, tbase);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (threadIdx.x < 32) tmem_dealloc(tbase, kTc05Cols);
 }
 
 // One-shot launch: grid = (gate groups, IPP chunks), one unit per CTA.

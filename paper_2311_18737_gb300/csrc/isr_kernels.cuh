@@ -11,12 +11,17 @@ namespace isr {
 isr_status fail(isr_status st, const char* fmt, ...);
 void clear_error();
 
+// radix orders: 0-2 Stockham, 3 warp-local, 4-5 paired FP32, 6-8 orders 0-2 with the inter-pass
+// twiddles in tensor memory
+constexpr int kNumOrders = 9;
+
 struct KernelEntry {
     const void* fn;   // __global__ integrate_kernel<LOG2N, TXT>
     const void* fn_full;  // the same for code_len == nfft (binary-phase codes only; else fn)
-    const void* fn_order[6];  // fn_full with radix order 0..5 (orders 1-3: nfft >= 2048, 4-5: 16384)
-    int smem_order[6];        // their shared memory
-    const void* fn_tc[5];     // [mode] tensor-core first pass (nfft 16384, binary phase); [0] unused
+    const void* fn_order[kNumOrders];  // fn_full with radix order 0..8 (1-3: nfft >= 2048; 4-8: 16384)
+    int smem_order[kNumOrders];        // their shared memory
+    const void* fn_tc[9];     // [mode] tensor-core first pass (nfft 16384, binary phase): 1-4 mma.sync,
+                              // 5-8 tcgen05; [0] unused
     int smem_tc;
     int smem;         // dynamic shared memory bytes
     int gates;        // range gates per CTA (G)
@@ -31,8 +36,9 @@ KernelEntry entry_for(int txt)
                   : txt == TX_C32  ? (const void*)integrate_kernel<L, TX_C32>
                                    : (const void*)integrate_kernel<L, TX_PM1>;
     const void* ff = txt == TX_PM1 ? (const void*)integrate_kernel<L, TX_PM1, true> : f;
-    KernelEntry e{f, ff, {ff, ff, ff, ff, ff, ff}, {S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM},
-                  {nullptr, nullptr, nullptr, nullptr, nullptr},
+    KernelEntry e{f, ff, {ff, ff, ff, ff, ff, ff, ff, ff, ff},
+                  {S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM},
+                  {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
                   0, S::SMEM, S::G, kThreads};
     if constexpr (L >= 11) {
         if (txt == TX_PM1) {
@@ -50,10 +56,20 @@ KernelEntry entry_for(int txt)
             e.smem_order[4] = SchedP::SMEM;
             e.fn_order[5] = (const void*)integrate_kernel_q<true>;
             e.smem_order[5] = SchedQ::SMEM;
+            e.fn_order[6] = (const void*)integrate_kernel_tm<14, TX_PM1, true, 0>;
+            e.smem_order[6] = Sched<14, 0, true>::SMEM;
+            e.fn_order[7] = (const void*)integrate_kernel_tm<14, TX_PM1, true, 1>;
+            e.smem_order[7] = Sched<14, 1, true>::SMEM;
+            e.fn_order[8] = (const void*)integrate_kernel_tm<14, TX_PM1, true, 2>;
+            e.smem_order[8] = Sched<14, 2, true>::SMEM;
             e.fn_tc[1] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_BF16_SPLIT>;
             e.fn_tc[2] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_FP16_SPLIT>;
             e.fn_tc[3] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_BF16>;
             e.fn_tc[4] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_FP16>;
+            e.fn_tc[5] = (const void*)integrate_kernel_tc05<P0_TC05_BF16_SPLIT>;
+            e.fn_tc[6] = (const void*)integrate_kernel_tc05<P0_TC05_FP16_SPLIT>;
+            e.fn_tc[7] = (const void*)integrate_kernel_tc05<P0_TC05_BF16>;
+            e.fn_tc[8] = (const void*)integrate_kernel_tc05<P0_TC05_FP16>;
             e.smem_tc = Sched<14, 1>::SMEM + kTcAfragBytes;
         }
     }

@@ -40,12 +40,20 @@ EXPORTS = ("isr_plan_create", "isr_integrate", "isr_spectra", "isr_plan_query", 
            "isr_est_features", "isr_est_grad", "isr_est_train_step", "isr_est_predict", "isr_est_destroy",
            "isr_batch_create", "isr_batch_run", "isr_batch_wait", "isr_batch_query", "isr_batch_destroy")
 
+# radix orders of isr_plan_set_order (4..8 at nfft 16384 with binary-phase codes only)
+N_ORDERS = 9
+
 ISR_PREC_FP32 = 0
 ISR_PREC_TC_BF16_SPLIT = 1
 ISR_PREC_TC_FP16_SPLIT = 2
 ISR_PREC_TC_BF16 = 3
 ISR_PREC_TC_FP16 = 4
-PRECISION_NAMES = {0: "fp32-simt", 1: "tc-bf16-split", 2: "tc-fp16-split", 3: "tc-bf16", 4: "tc-fp16"}
+ISR_PREC_TC05_BF16_SPLIT = 5
+ISR_PREC_TC05_FP16_SPLIT = 6
+ISR_PREC_TC05_BF16 = 7
+ISR_PREC_TC05_FP16 = 8
+PRECISION_NAMES = {0: "fp32-simt", 1: "tc-bf16-split", 2: "tc-fp16-split", 3: "tc-bf16", 4: "tc-fp16",
+                   5: "tc05-bf16-split", 6: "tc05-fp16-split", 7: "tc05-bf16", 8: "tc05-fp16"}
 
 ISR_BATCH_GRAPH = 1
 ISR_BATCH_AUTOTUNE = 2
@@ -418,7 +426,7 @@ class Plan:
                        max_chunks=self.desc.max_chunks, device=self.desc.device, stream=self.desc.stream)
         times = []
         try:
-            n_orders = 6 if (self.desc.nfft == 16384 and self.desc.tx_type == ISR_TX_PM1) else 4
+            n_orders = N_ORDERS if (self.desc.nfft == 16384 and self.desc.tx_type == ISR_TX_PM1) else 4
             for order in range(n_orders):
                 isr_plan_set_order(scratch.handle, order)
                 scratch.integrate(echo, tx_code, n_ipp)   # warm-up

@@ -1,5 +1,6 @@
 """Precision study: the first FFT pass on the tensor cores (BF16 / FP16, split or single
-products, FP32 accumulation) next to the FP32 SIMT path, at the realistic geometry.
+products, FP32 accumulation; the warp-level mma.sync engine and the tcgen05 engine) next to
+the FP32 SIMT path, at the realistic geometry.
 
 For each engine: integration speed, the per-bin relative difference from the FP32 SIMT
 engine on sampled gates over all IPPs, and the line position error of the peak fit against
@@ -43,7 +44,8 @@ def run(n_ipp: int = 10000, n_sample_gates: int = 8, reps: int = 2, seed: int = 
     sn = torch.empty(R, dtype=torch.float32, device=dev)
     results, spectra = {}, {}
     for mode in (isr.ISR_PREC_FP32, isr.ISR_PREC_TC_BF16_SPLIT, isr.ISR_PREC_TC_FP16_SPLIT, isr.ISR_PREC_TC_BF16,
-                 isr.ISR_PREC_TC_FP16):
+                 isr.ISR_PREC_TC_FP16, isr.ISR_PREC_TC05_BF16_SPLIT, isr.ISR_PREC_TC05_FP16_SPLIT,
+                 isr.ISR_PREC_TC05_BF16, isr.ISR_PREC_TC05_FP16):
         with isr.Plan(nfft=N, n_ranges=R, echo_stride=w.echo_stride, range_start=w.range_start,
                       range_step=w.range_step, tx_type=isr.ISR_TX_PM1, device=0, stream=stream) as plan:
             if mode == isr.ISR_PREC_FP32:

@@ -21,7 +21,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
 # every radix order Plan.autotune (and so bench.py) may pick at this workload
-ORDERS = [0, 1, 2, 3, 4, 5]
+ORDERS = list(range(isr.N_ORDERS))
 
 
 @pytest.fixture(scope="module")

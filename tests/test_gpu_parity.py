@@ -91,7 +91,8 @@ def test_per_ipp_code_rows_longer_than_the_code(log2n, kind):
     assert_parity(got, ref, what=f"{kind} tx_stride {nfft + 32} code_len {nfft}")
 
 
-@pytest.mark.parametrize("order,log2n", [(o, l) for l in (11, 12, 13, 14) for o in range(4)] + [(4, 14), (5, 14)])
+@pytest.mark.parametrize("order,log2n", [(o, l) for l in (11, 12, 13, 14) for o in range(4)] +
+                         [(o, 14) for o in range(4, isr.N_ORDERS)])
 def test_radix_orders(log2n, order):
     rng = np.random.default_rng(31 * log2n + order)
     nfft = 1 << log2n
@@ -116,7 +117,7 @@ def test_autotune_keeps_parity():
     with isr.Plan(nfft=nfft, n_ranges=R, echo_stride=echo.shape[1], range_step=25, device=0,
                   stream=torch.cuda.current_stream()) as plan:
         res = plan.autotune(e, t, P)
-        assert res["order"] in range(6) and len(res["ms"]) == 6
+        assert res["order"] in range(isr.N_ORDERS) and len(res["ms"]) == isr.N_ORDERS
         plan.integrate(e, t, P)
         out, n = plan.spectra()
     assert n == P
@@ -233,6 +234,22 @@ def test_ranges_override():
 # 16384: one gate per CTA (CTA barrier)
 @pytest.mark.parametrize("nfft", [1024, 4096, 16384])
 def test_timeout_is_reported_and_context_survives(nfft):
+    _timeout_case(nfft, 0)
+
+
+@pytest.mark.parametrize("order", [3, 6, 7])
+def test_timeout_every_barrier_kind_at_16384(order):
+    # warp-local schedule (CTA + warp barriers) and tensor-memory twiddles (the CTA frees its
+    # TMEM on the timeout path)
+    _timeout_case(16384, order)
+
+
+def test_timeout_with_the_tcgen05_first_pass():
+    # the dropped window is voted on before that IPP's GEMM is issued; the CTA frees its TMEM
+    _timeout_case(16384, 0, isr.ISR_PREC_TC05_FP16_SPLIT)
+
+
+def _timeout_case(nfft, order, precision=0):
     rng = np.random.default_rng(13)
     R, P = 4, 5
     echo, tx = _rand_case(rng, nfft, R, P, start=0, step=25, L=nfft, kind="pm1", per=False)
@@ -241,6 +258,10 @@ def test_timeout_is_reported_and_context_survives(nfft):
     t = torch.from_numpy(tx).to(dev)
     with isr.Plan(nfft=nfft, n_ranges=R, echo_stride=echo.shape[1], range_step=25, device=0,
                   stream=torch.cuda.current_stream()) as plan:
+        if order:
+            isr.isr_plan_set_order(plan.handle, order)
+        if precision:
+            isr.isr_plan_set_precision(plan.handle, precision)
         isr.isr_plan_set_wait_limit(plan.handle, 1 << 12)
         isr.isr_plan_test_drop_window(plan.handle, 2)
         plan.integrate(e, t, P)
@@ -250,7 +271,7 @@ def test_timeout_is_reported_and_context_survives(nfft):
         # the context is still usable: a clean integration on a fresh plan matches the oracle
     got, _ = gpu_integrate(echo, tx, nfft=nfft, n_ranges=R, range_step=25)
     ref = oracle.integrate(echo, tx, nfft=nfft, n_ranges=R, range_step=25)
-    assert_parity(got, ref, what="after timeout")
+    assert_parity(got, ref, what=f"after timeout (order {order})")
 
 
 def test_device_generator_matches_host_generator():

@@ -38,10 +38,12 @@ def case():
 # (relative 2^-22), so the FP32 tolerance holds; BF16 hi + lo carries 16 bits and the dropped
 # A_lo B_lo term is 2^-16 of a product, so a single IPP's power can be off by ~2 x 2^-16
 # (3e-5); averaging over IPPs shrinks it.
-BOUNDS = {isr.ISR_PREC_TC_FP16_SPLIT: RTOL, isr.ISR_PREC_TC_BF16_SPLIT: 5e-5}
+BOUNDS = {isr.ISR_PREC_TC_FP16_SPLIT: RTOL, isr.ISR_PREC_TC_BF16_SPLIT: 5e-5,
+          isr.ISR_PREC_TC05_FP16_SPLIT: RTOL, isr.ISR_PREC_TC05_BF16_SPLIT: 5e-5}
 
 
-@pytest.mark.parametrize("mode", [isr.ISR_PREC_TC_BF16_SPLIT, isr.ISR_PREC_TC_FP16_SPLIT])
+@pytest.mark.parametrize("mode", [isr.ISR_PREC_TC_BF16_SPLIT, isr.ISR_PREC_TC_FP16_SPLIT,
+                                  isr.ISR_PREC_TC05_BF16_SPLIT, isr.ISR_PREC_TC05_FP16_SPLIT])
 def test_split_modes_within_their_bounds(case, mode):
     echo, tx, R, start, step, ref = case
     mx, p99, med = assert_parity(_run(mode, echo, tx, R, start, step), ref, rtol=BOUNDS[mode],
@@ -49,13 +51,26 @@ def test_split_modes_within_their_bounds(case, mode):
     print(f"{isr.PRECISION_NAMES[mode]}: max {mx:.2e} p99 {p99:.2e} median {med:.2e}")
 
 
-def test_single_products_are_worse(case):
+@pytest.mark.parametrize("engine", ["mma.sync", "tcgen05"])
+def test_single_products_are_worse(case, engine):
     echo, tx, R, start, step, ref = case
-    err = {m: rel_err(_run(m, echo, tx, R, start, step), ref).max()
-           for m in (isr.ISR_PREC_TC_BF16_SPLIT, isr.ISR_PREC_TC_BF16, isr.ISR_PREC_TC_FP16)}
-    assert err[isr.ISR_PREC_TC_BF16] > 10 * err[isr.ISR_PREC_TC_BF16_SPLIT]
-    assert err[isr.ISR_PREC_TC_BF16] > err[isr.ISR_PREC_TC_FP16]
-    assert err[isr.ISR_PREC_TC_BF16] < 0.5
+    b_split, b_single, f_single = ((isr.ISR_PREC_TC_BF16_SPLIT, isr.ISR_PREC_TC_BF16, isr.ISR_PREC_TC_FP16)
+                                   if engine == "mma.sync" else
+                                   (isr.ISR_PREC_TC05_BF16_SPLIT, isr.ISR_PREC_TC05_BF16, isr.ISR_PREC_TC05_FP16))
+    err = {m: rel_err(_run(m, echo, tx, R, start, step), ref).max() for m in (b_split, b_single, f_single)}
+    assert err[b_single] > 10 * err[b_split]
+    assert err[b_single] > err[f_single]
+    assert err[b_single] < 0.5
+
+
+def test_tcgen05_and_mma_sync_engines_agree(case):
+    """Both tensor-core engines compute the same GEMM from the same split operands; only the
+    FP32 accumulation order inside the tensor core differs."""
+    echo, tx, R, start, step, ref = case
+    for a, b in ((isr.ISR_PREC_TC_FP16_SPLIT, isr.ISR_PREC_TC05_FP16_SPLIT),
+                 (isr.ISR_PREC_TC_BF16, isr.ISR_PREC_TC05_BF16)):
+        pa, pb = _run(a, echo, tx, R, start, step), _run(b, echo, tx, R, start, step)
+        assert rel_err(pb, pa).max() <= 2e-5, (isr.PRECISION_NAMES[a], isr.PRECISION_NAMES[b])
 
 
 def test_unsupported_shapes_rejected():
@@ -67,7 +82,8 @@ def test_unsupported_shapes_rejected():
 
 # per-bin bounds at the realistic geometry (sums over many IPPs); the single-product modes
 # carry the 16-bit rounding of the DFT matrix, a fixed error per bin that does not average out
-STUDY_BOUNDS = {"fp32-simt": RTOL, "tc-fp16-split": RTOL, "tc-bf16-split": 5e-5, "tc-fp16": 1e-3, "tc-bf16": 1e-2}
+STUDY_BOUNDS = {"fp32-simt": RTOL, "tc-fp16-split": RTOL, "tc-bf16-split": 5e-5, "tc-fp16": 1e-3, "tc-bf16": 1e-2,
+                "tc05-fp16-split": RTOL, "tc05-bf16-split": 5e-5, "tc05-fp16": 1e-3, "tc05-bf16": 1e-2}
 
 
 def test_study_against_fp64_oracle():
