@@ -37,8 +37,8 @@ METRIC = "range-gate spectra/sec (nfft=16384)"
 UNIT = "spectra/s"
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
 # sources that define the fused kernel and its launch (the recorded DRAM traffic is tied to them)
-TRAFFIC_SOURCES = ("isr_fft.cuh", "isr_kernel.cuh", "isr_tc.cuh", "isr_paired.cuh", "isr_kernels.cuh",
-                   "isr_k_16384.cu", "isr_api.cu")
+TRAFFIC_SOURCES = ("isr_fft.cuh", "isr_kernel.cuh", "isr_tc.cuh", "isr_tc05.cuh", "isr_tmem.cuh", "isr_paired.cuh",
+                   "isr_kernels.cuh", "isr_k_16384.cu", "isr_api.cu")
 
 
 def _peaks():

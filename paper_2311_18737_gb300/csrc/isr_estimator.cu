@@ -413,6 +413,191 @@ __global__ void __launch_bounds__(CF_THREADS) conv_tc_kernel(const void* __restr
     }
 }
 
+// ---------------------------------------------------------------- tcgen05 convolution
+// Layers 2-4 with BF16 storage on the fifth-generation tensor cores: the same GEMM as
+// conv_tc_kernel with positions as M,
+//   D[i][co] = sum_{k, ci} X[i + k - 4][ci] W[co][ci][k]     (M = 128 positions per tile, N = 32, K = 288),
+// issued by one thread as tcgen05.mma (kind::f16, BF16 operands from shared memory, FP32
+// accumulator in tensor memory).  The input tile is staged position-major in four "planes" of
+// eight channels, [rows][8 ch] with 16-byte rows, so every 8 x 16-byte core matrix of the
+// K-major no-swizzle layout is eight consecutive rows of one plane (SBO = 128 B between 8-row
+// groups, LBO = plane stride between the two 8-channel halves of a K = 16 step), and the A
+// operand of tap k is the same tile started k rows later: descriptor start + 16 k bytes.  The
+// weights are 36 planes [tap][8-channel group] of [32 co][8 ci].  Per CTA: 512 positions (four
+// M tiles, 18 MMAs each; the backward-data pass multiplies the hi and lo parts of its FP32 input,
+// 36 each), 128 TMEM columns; warp w reads tile w / 4 at its lane quarter and writes the
+// epilogue (bias + ReLU to BF16, or the FP32 gradient masked by the layer below) straight from
+// registers, one coalesced 32-position store per channel.
+constexpr int C5_CT = 512;                         // positions per CTA
+constexpr int C5_XW = C5_CT + KT - 1;              // staged rows (halo included)
+constexpr int C5_PLANE = C5_XW * 16 + 16;          // bytes per channel plane (+16: planes 4 banks apart)
+constexpr int C5_PART = 4 * C5_PLANE;              // one staged part (32 channels)
+constexpr int C5_WBYTES = KT * 4 * 512;            // weight planes
+constexpr int C5_COLS = 128;                       // TMEM columns: four tiles of N = 32
+constexpr size_t c5_smem_bytes(bool fwd) { return (size_t)(fwd ? 1 : 2) * C5_PART + C5_WBYTES + 16; }
+static_assert(C5_PLANE % 16 == 0 && (C5_PLANE / 4) % 32 == 4, "planes 16-byte aligned, four banks apart");
+
+// 16-bit index of (row j, channel c) in a staged part
+__device__ __forceinline__ int c5_idx(int j, int c) { return (c >> 3) * (C5_PLANE / 2) + j * 8 + (c & 7); }
+
+// Staging of one row's 32 channels, positions i0 - 4 + j for j < C5_XW (zero outside [0, L)),
+// into planes; the same reads as stage_act_tile, the stores at c5_idx.
+__device__ __forceinline__ void c5_stage_act(const unsigned short* __restrict__ rows, int L, int i0, unsigned short* xs)
+{
+    if ((L & 7) == 0) {
+        for (int e = threadIdx.x; e < CH * (C5_XW / 8 + 1); e += blockDim.x) {
+            const int c = e & (CH - 1), v = e / CH;
+            const int pos0 = i0 - 8 + 8 * v;
+            const unsigned short* src = rows + (size_t)c * L;
+            unsigned short t[8];
+            if (pos0 >= 0 && pos0 + 8 <= L) {
+                const uint4 q = *reinterpret_cast<const uint4*>(src + pos0);
+                const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    t[2 * k] = (unsigned short)(w[k] & 0xffffu);
+                    t[2 * k + 1] = (unsigned short)(w[k] >> 16);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) t[k] = (pos0 + k >= 0 && pos0 + k < L) ? src[pos0 + k] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int j = 8 * v - HALF + k;
+                if (j >= 0 && j < C5_XW) xs[c5_idx(j, c)] = t[k];
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < C5_XW * (CH / 2); e += blockDim.x) {
+            const int j = e / (CH / 2), cp = e - j * (CH / 2);
+            const int pos = i0 - HALF + j;
+            const size_t o = (size_t)(2 * cp) * L + pos;
+            const bool inside = pos >= 0 && pos < L;
+            const uint32_t v0 = inside ? rows[o] : 0u, v1 = inside ? rows[o + L] : 0u;
+            *reinterpret_cast<uint32_t*>(xs + c5_idx(j, 2 * cp)) = v0 | (v1 << 16);
+        }
+    }
+}
+
+// The same from FP32 rows, split into BF16 hi (part 0) and lo (part 1).
+__device__ __forceinline__ void c5_stage_split(const float* __restrict__ rows, int L, int i0, unsigned short* xh,
+                                               unsigned short* xl)
+{
+    for (int e = threadIdx.x; e < CH * (C5_XW / 4); e += blockDim.x) {
+        const int c = e & (CH - 1), v = e / CH;
+        const int pos0 = i0 - HALF + 4 * v;
+        const float* src = rows + (size_t)c * L;
+        float t[4];
+        if ((L & 3) == 0 && pos0 >= 0 && pos0 + 4 <= L) {
+            const float4 q = *reinterpret_cast<const float4*>(src + pos0);
+            t[0] = q.x; t[1] = q.y; t[2] = q.z; t[3] = q.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) t[k] = (pos0 + k >= 0 && pos0 + k < L) ? src[pos0 + k] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k += 2) {
+            uint32_t hi, lo;
+            isr::split2<true>(t[k], t[k + 1], hi, lo);
+            const int j = 4 * v + k;
+            xh[c5_idx(j, c)] = (unsigned short)(hi & 0xffffu);
+            xh[c5_idx(j + 1, c)] = (unsigned short)(hi >> 16);
+            xl[c5_idx(j, c)] = (unsigned short)(lo & 0xffffu);
+            xl[c5_idx(j + 1, c)] = (unsigned short)(lo >> 16);
+        }
+    }
+}
+
+// FWD: in = BF16 activations [B][32][L], out = BF16 relu(conv + bias).
+// !FWD: in = FP32 gradient [B][32][L], out = FP32 conv masked by mask > 0, no bias.
+// wt: GEMM rows [out channel][tap][in channel] (BF16), as for conv_tc_kernel.
+template <bool FWD>
+__global__ void __launch_bounds__(CF_THREADS) conv_tc05_kernel(const void* __restrict__ in,
+                                                               const __nv_bfloat16* __restrict__ wt,
+                                                               const float* __restrict__ bias,
+                                                               const __nv_bfloat16* __restrict__ mask, int L,
+                                                               void* __restrict__ out)
+{
+    constexpr int NX = FWD ? 1 : 2;
+    extern __shared__ __align__(128) unsigned char c5_smem[];
+    unsigned char* xs = c5_smem;                                  // NX parts of 4 planes
+    unsigned char* ws = c5_smem + NX * C5_PART;                   // 36 weight planes
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(ws + C5_WBYTES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(ws + C5_WBYTES + 8);
+    const int b = blockIdx.y, i0 = blockIdx.x * C5_CT;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) isr::mbar_init(isr::smem_u32(mbar), 1);
+    if (warp == 0) isr::tmem_alloc(isr::smem_u32(tslot), C5_COLS);
+    // weights: 16-byte piece (co, tap, 8-channel group g) of row co to plane (tap, g), row co
+    const uint4* w4 = reinterpret_cast<const uint4*>(wt);
+    for (int e = tid; e < CH * KT * 4; e += CF_THREADS) {
+        const int co = e / (KT * 4), r = e - co * (KT * 4);      // r = tap * 4 + g
+        *reinterpret_cast<uint4*>(ws + (r * CH + co) * 16) = w4[e];
+    }
+    if constexpr (FWD)
+        c5_stage_act(static_cast<const unsigned short*>(in) + (size_t)b * CH * L, L, i0,
+                     reinterpret_cast<unsigned short*>(xs));
+    else
+        c5_stage_split(static_cast<const float*>(in) + (size_t)b * CH * L, L, i0, reinterpret_cast<unsigned short*>(xs),
+                       reinterpret_cast<unsigned short*>(xs + C5_PART));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the tiles, for the tensor cores
+    isr::fence_barrier_init();
+    isr::tmem_fence_before_sync();
+    __syncthreads();
+    isr::tmem_fence_after_sync();
+    const uint32_t tbase = *tslot;
+
+    if (tid == 0) {
+        constexpr uint32_t idesc = isr::tc05_idesc<true>();      // BF16, FP32 accumulate, M 128, N 32
+        const uint32_t xa = isr::smem_u32(xs), wa = isr::smem_u32(ws);
+#pragma unroll 1
+        for (int m = 0; m < C5_CT / 128; ++m) {
+            uint32_t acc = 0;
+#pragma unroll 1
+            for (int part = 0; part < NX; ++part)
+#pragma unroll 1
+                for (int tap = 0; tap < KT; ++tap)
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        // rows 128 m + tap of the tile, channels 16 ks .. (planes 2 ks, 2 ks + 1)
+                        const uint64_t ad = isr::tc05_desc(xa + part * C5_PART + 2 * ks * C5_PLANE + (128 * m + tap) * 16,
+                                                           C5_PLANE, 128);
+                        const uint64_t bd = isr::tc05_desc(wa + (tap * 4 + 2 * ks) * 512, 512, 128);
+                        isr::tc05_mma(tbase + 32u * m, ad, bd, idesc, acc);
+                        acc = 1;
+                    }
+        }
+        isr::tc05_commit(isr::smem_u32(mbar));
+    }
+    const bool done = isr::mbar_wait(isr::smem_u32(mbar), 0, 1u << 26);
+    isr::tmem_fence_after_sync();
+
+    // epilogue: warp w, tile m = w / 4, lane quarter w % 4 -> position i
+    const int m = warp >> 2;
+    const int i = i0 + 128 * m + 32 * (warp & 3) + lane;
+    uint32_t r[32];
+    isr::tmem_ld32(isr::tmem_warp_lane_base(tbase) + 32u * m, r);
+    isr::tmem_wait_ld32(r);
+    if (done && i < L) {
+        const size_t row = (size_t)b * CH * L + i;
+#pragma unroll
+        for (int co = 0; co < CH; ++co) {
+            const float v = __uint_as_float(r[co]);
+            if constexpr (FWD) {
+                static_cast<__nv_bfloat16*>(out)[row + (size_t)co * L] = __float2bfloat16_rn(fmaxf(v + __ldg(bias + co), 0.f));
+            } else {
+                static_cast<float*>(out)[row + (size_t)co * L] = __bfloat162float(mask[row + (size_t)co * L]) > 0.f ? v : 0.f;
+            }
+        }
+    }
+    isr::tmem_fence_before_sync();
+    __syncthreads();
+    isr::tmem_fence_after_sync();
+    if (warp == 0) isr::tmem_dealloc(tbase, C5_COLS);
+}
+
 __device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], uint32_t addr)
 {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
@@ -988,6 +1173,7 @@ struct isr_est {
     int* zidx = nullptr;                      // ... and its first position
     bool weights_stale = true;                // the working weights need the master copy's values
     int wgrad_slots = 0;                      // resident tensor-core weight-gradient CTAs (all SMs)
+    bool conv05 = false;                      // BF16 convolutions on tcgen05 (else mma.sync)
     int* pidx = nullptr;
     float *da0 = nullptr, *da1 = nullptr; // gradient ping-pong [B][32][L]
 };
@@ -1031,6 +1217,10 @@ isr_status set_smem_attrs()
                                      (int)tc_smem_bytes(false)));
         EST_TRY(cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)wgrad_tc_smem_bytes()));
+        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)c5_smem_bytes(true)));
+        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)c5_smem_bytes(false)));
     }
     return ISR_OK;
 }
@@ -1055,9 +1245,13 @@ isr_status forward_t(isr_est* e, const float* x, int n, float* pos = nullptr, fl
     conv1_kernel<T><<<dim3((L + L1_CT - 1) / L1_CT, n), 256, 0, s>>>(act[0], wf, e->theta + OFF_B1, L, act[1]);
     for (int l = 2; l <= 4; ++l) {
         if constexpr (kTensorConv<T>) {
-            conv_tc_kernel<true><<<dim3((L + CF_CT - 1) / CF_CT, n), CF_THREADS, tc_smem_bytes(true), s>>>(
-                act[l - 1], static_cast<const T*>(e->tf) + (size_t)(l - 2) * CH * CH * KT, e->theta + b_off(l),
-                nullptr, L, act[l]);
+            const T* w = static_cast<const T*>(e->tf) + (size_t)(l - 2) * CH * CH * KT;
+            if (e->conv05)
+                conv_tc05_kernel<true><<<dim3((L + C5_CT - 1) / C5_CT, n), CF_THREADS, c5_smem_bytes(true), s>>>(
+                    act[l - 1], w, e->theta + b_off(l), nullptr, L, act[l]);
+            else
+                conv_tc_kernel<true><<<dim3((L + CF_CT - 1) / CF_CT, n), CF_THREADS, tc_smem_bytes(true), s>>>(
+                    act[l - 1], w, e->theta + b_off(l), nullptr, L, act[l]);
         } else {
             conv_kernel<T, T, T, T, CH, true><<<grid, 256, conv_smem_bytes(CH), s>>>(
                 act[l - 1], wf + CH * KT + (size_t)(l - 2) * CH * CH * KT, e->theta + b_off(l), nullptr, L, act[l]);
@@ -1101,10 +1295,15 @@ isr_status backward_t(isr_est* e, int n, const float* fpos, const float* pres)
             else
                 wgrad_kernel<T, CH><<<gw, 256, 0, s>>>(act[l - 1], da, L, e->grad + w_off(l), e->grad + b_off(l));
             // gradient into the layer below, masked by its ReLU: da_{l-1} = (W_l^T * da_l) (h_{l-1} > 0)
-            if constexpr (kTensorConv<T>)
-                conv_tc_kernel<false><<<dim3((L + CF_CT - 1) / CF_CT, n), CF_THREADS, tc_smem_bytes(false), s>>>(
-                    da, static_cast<const T*>(e->tb) + (size_t)(l - 2) * CH * CH * KT, nullptr, act[l - 1], L, dn);
-            else
+            if constexpr (kTensorConv<T>) {
+                const T* w = static_cast<const T*>(e->tb) + (size_t)(l - 2) * CH * CH * KT;
+                if (e->conv05)
+                    conv_tc05_kernel<false><<<dim3((L + C5_CT - 1) / C5_CT, n), CF_THREADS, c5_smem_bytes(false), s>>>(
+                        da, w, nullptr, act[l - 1], L, dn);
+                else
+                    conv_tc_kernel<false><<<dim3((L + CF_CT - 1) / CF_CT, n), CF_THREADS, tc_smem_bytes(false), s>>>(
+                        da, w, nullptr, act[l - 1], L, dn);
+            } else
                 conv_kernel<float, T, float, T, CH, false><<<gc, 256, conv_smem_bytes(CH), s>>>(
                     da, wbk + (size_t)(l - 2) * CH * CH * KT, nullptr, act[l - 1], L, dn);
             std::swap(da, dn);
@@ -1144,7 +1343,8 @@ isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t 
     *out = nullptr;
     if (nfft < 8 || band_lo < 0 || band_len < 16 || band_lo + band_len > nfft || max_batch < 1)
         return fail(ISR_ERR_INVALID_ARG, "need 0 <= band_lo, band_len >= 16, band_lo + band_len <= nfft, max_batch >= 1");
-    if (precision != ISR_EST_FP32 && precision != ISR_EST_BF16) return fail(ISR_ERR_UNSUPPORTED, "unknown precision");
+    if (precision != ISR_EST_FP32 && precision != ISR_EST_BF16 && precision != ISR_EST_BF16_MMASYNC)
+        return fail(ISR_ERR_UNSUPPORTED, "unknown precision");
     int dev = device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(ISR_ERR_CUDA, "no current device");
     Dev guard(dev);
@@ -1155,9 +1355,11 @@ isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t 
     e->L = band_len;
     e->max_batch = max_batch;
     e->precision = precision;
+    e->conv05 = precision == ISR_EST_BF16;
     e->dev = dev;
     e->stream = static_cast<cudaStream_t>(stream);
-    const size_t es = precision == ISR_EST_BF16 ? 2 : 4;
+    const bool bf16 = precision != ISR_EST_FP32;
+    const size_t es = bf16 ? 2 : 4;
     const size_t B = max_batch, L = band_len;
     cudaError_t r = cudaSuccess;
     auto A = [&](void** p, size_t bytes) {
@@ -1169,7 +1371,7 @@ isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t 
     A((void**)&e->grad, 4 * NPARAM);
     A(&e->wf, es * (CH * KT + 3 * CH * CH * KT));
     A(&e->wb, es * 3 * CH * CH * KT);
-    if (precision == ISR_EST_BF16) {
+    if (bf16) {
         A(&e->tf, es * 3 * CH * CH * KT);
         A(&e->tb, es * 3 * CH * CH * KT);
     }
@@ -1195,12 +1397,12 @@ isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t 
     if (r == cudaSuccess) r = cudaMemset(e->m, 0, 4 * NPARAM);
     if (r == cudaSuccess) r = cudaMemset(e->v, 0, 4 * NPARAM);
     if (r == cudaSuccess) {
-        isr_status st = precision == ISR_EST_BF16 ? set_smem_attrs<__nv_bfloat16>() : set_smem_attrs<float>();
+        isr_status st = bf16 ? set_smem_attrs<__nv_bfloat16>() : set_smem_attrs<float>();
         if (st != ISR_OK) {
             isr_est_destroy(e);
             return st;
         }
-        if (precision == ISR_EST_BF16) {
+        if (bf16) {
             int sms = 0, occ = 0;
             r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (r == cudaSuccess)
@@ -1255,9 +1457,9 @@ isr_status isr_est_grad(isr_est* e, const float* x, int32_t n, const float* line
     if (st != ISR_OK) return st;
     if (!line_bin || !present) return fail(ISR_ERR_INVALID_ARG, "labels must not be NULL");
     Dev guard(e->dev);
-    st = e->precision == ISR_EST_BF16 ? forward_t<__nv_bfloat16>(e, x, n) : forward_t<float>(e, x, n);
+    st = e->precision != ISR_EST_FP32 ? forward_t<__nv_bfloat16>(e, x, n) : forward_t<float>(e, x, n);
     if (st == ISR_OK)
-        st = e->precision == ISR_EST_BF16 ? backward_t<__nv_bfloat16>(e, n, line_bin, present)
+        st = e->precision != ISR_EST_FP32 ? backward_t<__nv_bfloat16>(e, n, line_bin, present)
                                           : backward_t<float>(e, n, line_bin, present);
     if (st != ISR_OK) return st;
     if (grad) EST_TRY(cudaMemcpyAsync(grad, e->grad, 4 * NPARAM, cudaMemcpyDefault, e->stream));
@@ -1273,9 +1475,9 @@ isr_status isr_est_train_step(isr_est* e, const float* x, int32_t n, const float
     if (st != ISR_OK) return st;
     if (!line_bin || !present || !(lr > 0.f)) return fail(ISR_ERR_INVALID_ARG, "labels NULL or lr <= 0");
     Dev guard(e->dev);
-    st = e->precision == ISR_EST_BF16 ? forward_t<__nv_bfloat16>(e, x, n) : forward_t<float>(e, x, n);
+    st = e->precision != ISR_EST_FP32 ? forward_t<__nv_bfloat16>(e, x, n) : forward_t<float>(e, x, n);
     if (st == ISR_OK)
-        st = e->precision == ISR_EST_BF16 ? backward_t<__nv_bfloat16>(e, n, line_bin, present)
+        st = e->precision != ISR_EST_FP32 ? backward_t<__nv_bfloat16>(e, n, line_bin, present)
                                           : backward_t<float>(e, n, line_bin, present);
     if (st != ISR_OK) return st;
     e->step += 1;
@@ -1298,7 +1500,7 @@ isr_status isr_est_predict(isr_est* e, const float* x, int32_t n, float* line_bi
     if (st != ISR_OK) return st;
     if (!line_bin || !presence) return fail(ISR_ERR_INVALID_ARG, "outputs must not be NULL");
     Dev guard(e->dev);
-    return e->precision == ISR_EST_BF16 ? forward_t<__nv_bfloat16>(e, x, n, line_bin, presence)
+    return e->precision != ISR_EST_FP32 ? forward_t<__nv_bfloat16>(e, x, n, line_bin, presence)
                                         : forward_t<float>(e, x, n, line_bin, presence);
 }
 

@@ -177,4 +177,117 @@ struct BitRev {
     __host__ __device__ static constexpr int at(int q) { return bitrev(q, bits); }
 };
 
+// ---------------------------------------------------------------- scaled radix-2^2 DFT
+// The same network as dif22_stage, with every non-trivial twiddle product in tangent form:
+// z (c - i s) = c (z.x + t z.y, z.y - t z.x) with t = s / c when |c| >= |s|, else
+// s (t' z.x + z.y, t' z.y - z.x) with t' = c / s -- two FMAs instead of four instructions --
+// and the real factor (c or s) left out of the stored value.  Each value then carries a
+// compile-time factor that turns it into the true value; butterflies of values with unequal
+// factors add with one FMA by the factor ratio (a plain add where the ratio is +-1).  The
+// output X[q] of sdft<R> equals kappa_q * v[bitrev(q)] with kappa_q = ScaleNet<R>::out(q).
+namespace sdft_detail {
+// factor that tw_mul<I, LEN> leaves out of its result
+__host__ __device__ constexpr double tw_factor(int I, int LEN)
+{
+    const int i = ((I % LEN) + LEN) % LEN;
+    if (i == 0 || 4 * i == LEN) return 1.0;      // identity, -i (component swap)
+    if (2 * i == LEN || 4 * i == 3 * LEN) return -1.0;   // -1, +i (sign left in the factor)
+    const double c = ct_cos2pi(i, LEN), s = ct_sin2pi(i, LEN);
+    const double ac = c < 0 ? -c : c, as = s < 0 ? -s : s;
+    return ac >= as ? c : s;
+}
+}  // namespace sdft_detail
+
+template <int R>
+struct ScaleNet {
+    static constexpr int LEVELS = ilog2(R) / 2 + (ilog2(R) & 1);
+    double sc[LEVELS + 1][R];   // factor of v[i] after each level (level 0: the inputs)
+    __host__ __device__ constexpr ScaleNet() : sc{}
+    {
+        for (int i = 0; i < R; ++i) sc[0][i] = 1.0;
+        int l = 0;
+        for (int LEN = R; LEN >= 2; LEN /= 4, ++l) {
+            for (int i = 0; i < R; ++i) sc[l + 1][i] = sc[l][i];
+            if (LEN == 2) {
+                for (int s = 0; s < R; s += 2) sc[l + 1][s + 1] = sc[l][s];
+            } else {
+                const int Q = LEN / 4;
+                for (int s = 0; s < R; s += LEN)
+                    for (int i = 0; i < Q; ++i) {
+                        const double s0 = sc[l][s + i];
+                        sc[l + 1][s + i] = s0;
+                        sc[l + 1][s + i + Q] = s0 * sdft_detail::tw_factor(2 * i, LEN);
+                        sc[l + 1][s + i + 2 * Q] = s0 * sdft_detail::tw_factor(i, LEN);
+                        sc[l + 1][s + i + 3 * Q] = s0 * sdft_detail::tw_factor(3 * i, LEN);
+                    }
+            }
+        }
+    }
+    // factor of output X[q] (stored at v[bitrev(q)])
+    __host__ __device__ constexpr double out(int q) const { return sc[LEVELS][bitrev(q, ilog2(R))]; }
+};
+
+// z (c - i s) for W = exp(-2 pi i I / LEN), up to the factor tw_factor(I, LEN)
+template <int I, int LEN>
+__device__ __forceinline__ float2 tw_mul(float2 z)
+{
+    constexpr int i = ((I % LEN) + LEN) % LEN;
+    if constexpr (i == 0 || 2 * i == LEN) {
+        return z;
+    } else if constexpr (4 * i == LEN || 4 * i == 3 * LEN) {
+        return make_float2(z.y, -z.x);
+    } else {
+        constexpr double c = ct_cos2pi(i, LEN), s = ct_sin2pi(i, LEN);
+        constexpr bool cform = (c < 0 ? -c : c) >= (s < 0 ? -s : s);
+        constexpr float t = cform ? float(s / c) : float(c / s);
+        if constexpr (cform) return make_float2(fmaf(t, z.y, z.x), fmaf(-t, z.x, z.y));
+        else return make_float2(fmaf(t, z.x, z.y), fmaf(t, z.y, -z.x));
+    }
+}
+
+template <int R, int LEN, int L>
+__device__ __forceinline__ void sdif22_stage(float2* v)
+{
+    constexpr ScaleNet<R> net{};
+    if constexpr (LEN == 2) {
+        static_for<R / 2>([&](auto Sb) {
+            constexpr int s = 2 * decltype(Sb)::value;
+            constexpr float r = float(net.sc[L][s + 1] / net.sc[L][s]);
+            const float2 a = v[s], b = v[s + 1];
+            v[s] = make_float2(fmaf(r, b.x, a.x), fmaf(r, b.y, a.y));
+            v[s + 1] = make_float2(fmaf(-r, b.x, a.x), fmaf(-r, b.y, a.y));
+        });
+    } else {
+        constexpr int Q = LEN / 4;
+        static_for<R / LEN>([&](auto Sb) {
+            constexpr int s = decltype(Sb)::value * LEN;
+            static_for<Q>([&](auto Iv) {
+                constexpr int i = decltype(Iv)::value;
+                constexpr double s0 = net.sc[L][s + i], s1 = net.sc[L][s + i + Q];
+                constexpr float r20 = float(net.sc[L][s + i + 2 * Q] / s0);
+                constexpr float r31 = float(net.sc[L][s + i + 3 * Q] / s1);
+                constexpr float r10 = float(s1 / s0);
+                const float2 x0 = v[s + i], x1 = v[s + i + Q], x2 = v[s + i + 2 * Q], x3 = v[s + i + 3 * Q];
+                const float2 a0 = make_float2(fmaf(r20, x2.x, x0.x), fmaf(r20, x2.y, x0.y));
+                const float2 d0 = make_float2(fmaf(-r20, x2.x, x0.x), fmaf(-r20, x2.y, x0.y));
+                const float2 a1 = make_float2(fmaf(r31, x3.x, x1.x), fmaf(r31, x3.y, x1.y));
+                const float2 d1 = make_float2(fmaf(-r31, x3.x, x1.x), fmaf(-r31, x3.y, x1.y));
+                v[s + i] = make_float2(fmaf(r10, a1.x, a0.x), fmaf(r10, a1.y, a0.y));
+                v[s + i + Q] = tw_mul<2 * i, LEN>(make_float2(fmaf(-r10, a1.x, a0.x), fmaf(-r10, a1.y, a0.y)));
+                // d0 - i d1 and d0 + i d1, d1 weighted by r10
+                v[s + i + 2 * Q] = tw_mul<i, LEN>(make_float2(fmaf(r10, d1.y, d0.x), fmaf(-r10, d1.x, d0.y)));
+                v[s + i + 3 * Q] = tw_mul<3 * i, LEN>(make_float2(fmaf(-r10, d1.y, d0.x), fmaf(r10, d1.x, d0.y)));
+            });
+        });
+        if constexpr (LEN > 4) sdif22_stage<R, LEN / 4, L + 1>(v);
+    }
+}
+
+// Scaled R-point forward DFT of v[0..R): X[q] = ScaleNet<R>{}.out(q) * v[bitrev(q)].
+template <int R>
+__device__ __forceinline__ void sdft(float2* v)
+{
+    if constexpr (R > 1) sdif22_stage<R, R, 0>(v);
+}
+
 }  // namespace isr

@@ -381,6 +381,16 @@ __device__ __forceinline__ void twiddle_tmem(float2* u, uint32_t addr)
     });
 }
 
+// R-point DFT of a pass of the fused unit: from nfft 1024 up the tangent-form radix-2^2 network
+// (sdft: two instead of four instructions per non-trivial twiddle product, same outputs), below
+// it the plain radix-2 network, which measured faster there
+template <int R, int LOG2N>
+__device__ __forceinline__ void unit_dft(float2* u)
+{
+    if constexpr (LOG2N >= 10 && R >= 8) sdft<R>(u);
+    else dft<R, LOG2N >= 10>(u);
+}
+
 // ---------------------------------------------------------------- debug-build window check
 // With -DISR_DEBUG every gate checks, before it stages anything, that its window copy lies
 // inside the echo row (s_r >= 0, s_r + code_len <= echo_stride, the 16-byte-rounded copy
@@ -620,7 +630,7 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
                 if (FULL || pos < a.code_len)
                     u[k] = decode<TXT>(stage[off + pos], txrow, pos, (signs << (31 - (b * R0 + k))) & 0x80000000u);
             });
-            dft<R0, LOG2N >= 10>(u);
+            unit_dft<R0, LOG2N>(u);
             if constexpr (NP == 1) {
                 static_for<R0>([&](auto Qc) {
                     constexpr int q = decltype(Qc)::value;
@@ -664,7 +674,7 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
                 else if constexpr (S::tab(1) && R >= 16) twiddle_tab3<R, NS>(u, tab, j % NS);
                 else if constexpr (S::tab(1)) twiddle_tab<R, NS>(u, tab, j % NS);
                 else twiddle<R>(u, twb[b * T + t]);
-                dft<R, LOG2N >= 10>(u);
+                unit_dft<R, LOG2N>(u);
                 store_strided<N / R, R, S::PADP>(xch, j, u);
             });
             gsync();
@@ -679,7 +689,7 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
                 if constexpr (S::tab(1) && R >= 16) twiddle_tab3<R, NS>(u, tab, j % NS);
                 else if constexpr (S::tab(1)) twiddle_tab<R, NS>(u, tab, j % NS);
                 else twiddle<R>(u, twb[b * T + t]);
-                dft<R, LOG2N >= 10>(u);
+                unit_dft<R, LOG2N>(u);
             });
             gsync();
             static_for<E / R>([&](auto Bc) {
@@ -712,7 +722,7 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
                 else if constexpr (S::tab(PL) && R >= 16) twiddle_tab3<R, S::ns(PL)>(u, tab + TAB0, j % S::ns(PL));
                 else if constexpr (S::tab(PL)) twiddle_tab<R, S::ns(PL)>(u, tab + TAB0, j % S::ns(PL));
                 else twiddle<R>(u, twb[(SLOT0 + b) * T + t]);
-                dft<R, LOG2N >= 10>(u);
+                unit_dft<R, LOG2N>(u);
                 static_for<R>([&](auto Qc) {
                     constexpr int q = decltype(Qc)::value;
                     float2 X = u[BitRev<R>::at(q)];
@@ -874,7 +884,7 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
                 if (FULL || pos < a.code_len)
                     u[k] = decode<TXT>(stage[off + pos], txrow, pos, (signs << (31 - (b * M + k))) & 0x80000000u);
             });
-            dft<M, true>(u);
+            sdft<M>(u);
             const float2 w = twb[b * T + t];
             float2 cur = w;
             static_for<M>([&](auto Qc) {
@@ -903,7 +913,7 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
             constexpr int k = decltype(Kc)::value;
             v[k] = rw[lane + 34 * k];
         });
-        dft<32, true>(v);
+        sdft<32>(v);
         __syncwarp();
         static_for<16>([&](auto Qc) {                       // y[32 l + q], q pairs: rw[34 l + q]
             constexpr int q = 2 * decltype(Qc)::value;
@@ -917,7 +927,7 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
             v[k] = rw[lane + 34 * k];
         });
         twiddle_tab3<32, 32>(v, tabc, lane);
-        dft<32, true>(v);
+        sdft<32>(v);
         static_for<32>([&](auto Qc) {
             constexpr int q = decltype(Qc)::value;
             const float2 X = v[BitRev<32>::at(q)];

@@ -61,6 +61,7 @@ ISR_BATCH_AUTOTUNE = 2
 ISR_EST_N_PARAMS = 30210
 ISR_EST_FP32 = 0
 ISR_EST_BF16 = 1
+ISR_EST_BF16_MMASYNC = 2
 
 # floats of the allocation-free variant's file-scope scratch array
 ISR_STATIC_SCRATCH_FLOATS = 4 * 1024 * 1024

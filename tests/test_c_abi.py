@@ -56,7 +56,7 @@ def test_constants_match_the_binding(tmp_path):
              "ISR_ERR_CUDA", "ISR_ERR_TIMEOUT", "ISR_TX_CI16", "ISR_TX_C32", "ISR_TX_PM1", "ISR_RESET_AFTER",
              "ISR_MEAN", "ISR_PREC_FP32", "ISR_PREC_TC_BF16_SPLIT", "ISR_PREC_TC_FP16_SPLIT", "ISR_PREC_TC_BF16",
              "ISR_PREC_TC_FP16", "ISR_PREC_TC05_BF16_SPLIT", "ISR_PREC_TC05_FP16_SPLIT",
-             "ISR_PREC_TC05_BF16", "ISR_PREC_TC05_FP16", "ISR_STATIC_SCRATCH_FLOATS", "ISR_EST_N_PARAMS", "ISR_EST_FP32", "ISR_EST_BF16",
+             "ISR_PREC_TC05_BF16", "ISR_PREC_TC05_FP16", "ISR_STATIC_SCRATCH_FLOATS", "ISR_EST_N_PARAMS", "ISR_EST_FP32", "ISR_EST_BF16", "ISR_EST_BF16_MMASYNC",
              "ISR_BATCH_GRAPH", "ISR_BATCH_AUTOTUNE"]
     body = "\n".join(f'    printf("{n} %lld\\n", (long long)({n}));' for n in names)
     src.write_text(f'#include <stdio.h>\n#include "isr.h"\nint main(void)\n{{\n{body}\n    return 0;\n}}\n')

@@ -52,7 +52,34 @@ def test_bf16_storage_close_to_reference():
     e.close()
 
 
-def _dyadic_case(B=4, L=600, seed=7):
+@pytest.mark.parametrize("precision", [isr.ISR_EST_BF16, isr.ISR_EST_BF16_MMASYNC])
+def test_bf16_gradients_per_block_against_rounding_reference(precision):
+    """Random inputs (not dyadic): the BF16 variant against the FP64 reference that rounds to
+    BF16 exactly where the variant stores (input, conv weights, activations).  What is left is
+    FP32 accumulation order and the hi + lo split of the gradient entering the backward passes
+    (~16 significant bits), which can move an activation across a BF16 rounding boundary now and
+    then; so every parameter block's gradient must agree in norm to 2 % and in direction to
+    cosine 0.999, and the loss to 1e-3."""
+    e, theta, x, f, y, (xd, fd, yd) = _setup(precision, seed=3)
+    loss, g = e.grad(xd, fd, yd)
+    rl, rg = ref.loss_and_grad(theta.astype(np.float64), x, f, y, store=ref.round_bf16)
+    assert abs(loss - rl) <= 1e-3 * abs(rl), (loss, rl)
+    gd, rd = ref.unpack(g.astype(np.float64)), ref.unpack(rg)
+    gmax = np.abs(rg).max()
+    for name, _ in ref.SHAPES:
+        a, b = gd[name].ravel(), rd[name].ravel()
+        nb = np.linalg.norm(b)
+        if nb <= 1e-3 * gmax:
+            # b5: exactly zero in exact arithmetic; bound it by the overall gradient scale
+            assert np.abs(a).max() <= 1e-3 * gmax, name
+            continue
+        rel = np.linalg.norm(a - b) / nb
+        cos = float(a @ b / (np.linalg.norm(a) * nb))
+        assert rel <= 2e-2 and cos >= 0.999, f"{name}: relative error {rel:.2e}, cosine {cos:.6f}"
+    e.close()
+
+
+def _dyadic_case(B=4, L=600, seed=7, precision=isr.ISR_EST_BF16):
     """Conv weights and biases in multiples of 1/8 within [-1/4, 1/4] and inputs in multiples
     of 1/4: every product and FP32 partial sum of the convolutions is exact, so the BF16
     variant's activations are the BF16 roundings of exact values on both sides.  L = 600 spans
@@ -66,16 +93,23 @@ def _dyadic_case(B=4, L=600, seed=7):
     x = (rng.integers(-8, 9, (B, L)) / 4.0).astype(np.float32)
     f = rng.uniform(3, L - 3, B).astype(np.float32)
     y = np.array([1, 0, 1, 1][:B], dtype=np.float32)
-    e = est_mod.Estimator(max_batch=8, precision=isr.ISR_EST_BF16, nfft=1024, band_lo=0, band_len=L)
+    e = est_mod.Estimator(max_batch=8, precision=precision, nfft=2048, band_lo=0, band_len=L)
     e.set_params(theta)
     dev = torch.device("cuda:0")
     return e, theta, x, f, y, [torch.from_numpy(a).to(dev) for a in (x, f, y)]
 
 
-# 600: two full 256-position tiles and a ragged third; 37: odd (unpaired stores), one partial tile
-@pytest.mark.parametrize("L", [600, 37])
-def test_bf16_tensor_core_forward_matches_bf16_storage_reference(L):
-    e, theta, x, f, y, (xd, fd, yd) = _dyadic_case(L=L)
+# Both BF16 convolution engines: tcgen05 (512-position CTAs of four M = 128 tiles) and mma.sync
+# (256/512-position tiles).  600: full tiles and a ragged rest; 37: odd (unpaired stores), one
+# partial tile; 1100: three tcgen05 CTAs with a length that is not a multiple of 8 (the
+# word-by-word staging path).
+ENGINES = [isr.ISR_EST_BF16, isr.ISR_EST_BF16_MMASYNC]
+
+
+@pytest.mark.parametrize("precision", ENGINES)
+@pytest.mark.parametrize("L", [600, 37, 1100])
+def test_bf16_tensor_core_forward_matches_bf16_storage_reference(L, precision):
+    e, theta, x, f, y, (xd, fd, yd) = _dyadic_case(L=L, precision=precision)
     pos, pres = e.predict(xd)
     rpos, rpres = ref.predict(theta.astype(np.float64), x, store=ref.round_bf16)
     assert np.abs(pos.cpu().numpy() - rpos).max() <= 1e-3
@@ -83,11 +117,12 @@ def test_bf16_tensor_core_forward_matches_bf16_storage_reference(L):
     e.close()
 
 
-@pytest.mark.parametrize("L", [600, 37])
-def test_bf16_tensor_core_gradients_match_bf16_storage_reference(L):
+@pytest.mark.parametrize("precision", ENGINES)
+@pytest.mark.parametrize("L", [600, 37, 1100])
+def test_bf16_tensor_core_gradients_match_bf16_storage_reference(L, precision):
     """The backward-data convolution splits the FP32 gradient into two BF16 parts (~16
     significant bits): every parameter block within 1e-3 of its largest gradient."""
-    e, theta, x, f, y, (xd, fd, yd) = _dyadic_case(L=L, seed=8)
+    e, theta, x, f, y, (xd, fd, yd) = _dyadic_case(L=L, seed=8, precision=precision)
     loss, g = e.grad(xd, fd, yd)
     rl, rg = ref.loss_and_grad(theta.astype(np.float64), x, f, y, store=ref.round_bf16)
     assert abs(loss - rl) <= 1e-4 * abs(rl)
