@@ -140,7 +140,7 @@ isr_status isr_plan_set_profiling(isr_plan* plan, int32_t enable);
  * and return; the next isr_spectra reports ISR_ERR_TIMEOUT.  polls must be > 0. */
 isr_status isr_plan_set_wait_limit(isr_plan* plan, uint32_t polls);
 
-/* Radix order (0..8) of the kernel used for binary-phase codes with code_len == nfft, for
+/* Radix order (0..9) of the kernel used for binary-phase codes with code_len == nfft, for
  * nfft >= 2048 (smaller sizes have one order): 0..2 are three-pass Stockham orders, 3 is a
  * radix-(nfft/1024) decimation-in-frequency pass followed by one 1024-point transform per
  * warp; 4 and 5 (nfft 16384 only) use paired FP32 instructions (two operations each):
@@ -149,8 +149,9 @@ isr_status isr_plan_set_wait_limit(isr_plan* plan, uint32_t polls);
  * and each radix-32 butterfly split into two paired 16-point halves; 6, 7 and 8 (nfft
  * 16384 only) are orders 0, 1 and 2 with every thread's inter-pass twiddles computed once
  * per CTA into tensor memory (all 512 columns of the SM's TMEM, freed when the CTA ends)
- * instead of being formed from tables and recurrences in every IPP.  Every order gives
- * the same spectra up to FP32 rounding; they differ in speed, so a caller (or the
+ * instead of being formed from tables and recurrences in every IPP; 9 (nfft 16384 only) is
+ * order 3 with its twiddles in tensor memory likewise and unit-stride first-pass columns.
+ * Every order gives the same spectra up to FP32 rounding; they differ in speed, so a caller (or the
  * binding's autotuner) may time them and keep the fastest.  Default 0. */
 isr_status isr_plan_set_order(isr_plan* plan, int32_t order);
 

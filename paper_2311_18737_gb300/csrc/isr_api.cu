@@ -525,7 +525,7 @@ isr_status isr_plan_set_order(isr_plan* p, int32_t order)
         return fail(ISR_ERR_INVALID_ARG, "plan is NULL or order not in 0..%d", isr::kNumOrders - 1);
     if (p->d.nfft < 2048 && order != 0) return fail(ISR_ERR_UNSUPPORTED, "radix orders exist for nfft >= 2048 only");
     if (order >= 4 && (p->d.nfft != 16384 || p->d.tx_type != ISR_TX_PM1))
-        return fail(ISR_ERR_UNSUPPORTED, "radix orders 4 to 8 exist for nfft 16384 with ISR_TX_PM1 only");
+        return fail(ISR_ERR_UNSUPPORTED, "radix orders 4 to 9 exist for nfft 16384 with ISR_TX_PM1 only");
     p->order = order;
     return ISR_OK;
 }

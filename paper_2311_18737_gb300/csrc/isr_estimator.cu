@@ -423,49 +423,74 @@ __global__ void __launch_bounds__(CF_THREADS) conv_tc_kernel(const void* __restr
 // K-major no-swizzle layout is eight consecutive rows of one plane (SBO = 128 B between 8-row
 // groups, LBO = plane stride between the two 8-channel halves of a K = 16 step), and the A
 // operand of tap k is the same tile started k rows later: descriptor start + 16 k bytes.  The
-// weights are 36 planes [tap][8-channel group] of [32 co][8 ci].  Per CTA: 512 positions (four
-// M tiles, 18 MMAs each; the backward-data pass multiplies the hi and lo parts of its FP32 input,
-// 36 each), 128 TMEM columns; warp w reads tile w / 4 at its lane quarter and writes the
-// epilogue (bias + ReLU to BF16, or the FP32 gradient masked by the layer below) straight from
-// registers, one coalesced 32-position store per channel.
-constexpr int C5_CT = 512;                         // positions per CTA
-constexpr int C5_XW = C5_CT + KT - 1;              // staged rows (halo included)
-constexpr int C5_PLANE = C5_XW * 16 + 16;          // bytes per channel plane (+16: planes 4 banks apart)
-constexpr int C5_PART = 4 * C5_PLANE;              // one staged part (32 channels)
-constexpr int C5_WBYTES = KT * 4 * 512;            // weight planes
-constexpr int C5_COLS = 128;                       // TMEM columns: four tiles of N = 32
-constexpr size_t c5_smem_bytes(bool fwd) { return (size_t)(fwd ? 1 : 2) * C5_PART + C5_WBYTES + 16; }
-static_assert(C5_PLANE % 16 == 0 && (C5_PLANE / 4) % 32 == 4, "planes 16-byte aligned, four banks apart");
+// weights are 36 planes [tap][8-channel group] of [32 co][8 ci].  Per CTA: TPC M tiles of 128
+// positions (128 TPC threads; 18 MMAs per tile, 36 in the backward-data pass, which multiplies the
+// hi and lo parts of its FP32 input) and 32 TPC TMEM columns; warp w reads tile w / 4 at its lane
+// quarter and writes the epilogue (bias + ReLU to BF16, or the FP32 gradient masked by the layer
+// below) straight from registers, one coalesced 32-position store per channel.  Every thread
+// issues all of its staging loads before its first shared store.
+// TPC = M tiles of 128 positions per CTA (1, 2 or 4): 128 TPC threads, four warps per tile
+template <int TPC> struct C5 {
+    static constexpr int CT = 128 * TPC;                   // positions per CTA
+    static constexpr int THREADS = 128 * TPC;
+    static constexpr int XW = CT + KT - 1;                 // staged rows (halo included)
+    static constexpr int PLANE = XW * 16 + 16;             // bytes per channel plane (+16: planes 4 banks apart)
+    static constexpr int PART = 4 * PLANE;                 // one staged part (32 channels)
+    static constexpr int COLS = TPC <= 1 ? 32 : 32 * TPC;  // TMEM columns: one N = 32 tile per M tile
+    static constexpr size_t smem(bool fwd) { return (size_t)(fwd ? 1 : 2) * PART + KT * 4 * 512 + 16; }
+    static_assert(PLANE % 16 == 0 && (PLANE / 4) % 32 == 4, "planes 16-byte aligned, four banks apart");
+};
+constexpr int C5_WBYTES = KT * 4 * 512;                    // weight planes
+constexpr int C5_TPC = 2;                                  // the launched shape
 
-// 16-bit index of (row j, channel c) in a staged part
-__device__ __forceinline__ int c5_idx(int j, int c) { return (c >> 3) * (C5_PLANE / 2) + j * 8 + (c & 7); }
+// 16-bit index of (row j, channel c) in a staged part of plane size PLANE bytes
+template <int PLANE>
+__device__ __forceinline__ int c5_idx(int j, int c) { return (c >> 3) * (PLANE / 2) + j * 8 + (c & 7); }
 
 // Staging of one row's 32 channels, positions i0 - 4 + j for j < C5_XW (zero outside [0, L)),
-// into planes; the same reads as stage_act_tile, the stores at c5_idx.
+// into planes: the same pieces as stage_act_tile, but every thread issues all of its global loads
+// before its first shared store (the loads come from L2 and would otherwise be waited on one by
+// one).  Called by CF_THREADS threads.
+template <int TPC>
 __device__ __forceinline__ void c5_stage_act(const unsigned short* __restrict__ rows, int L, int i0, unsigned short* xs)
 {
+    using G = C5<TPC>;
+    constexpr int C5_XW = G::XW, CF_THREADS = G::THREADS, P = G::PLANE;
     if ((L & 7) == 0) {
-        for (int e = threadIdx.x; e < CH * (C5_XW / 8 + 1); e += blockDim.x) {
+        constexpr int NITEM = CH * (C5_XW / 8 + 1), PER = (NITEM + CF_THREADS - 1) / CF_THREADS;
+        uint4 q[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = threadIdx.x + u * CF_THREADS;
             const int c = e & (CH - 1), v = e / CH;
             const int pos0 = i0 - 8 + 8 * v;
-            const unsigned short* src = rows + (size_t)c * L;
+            q[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (e < NITEM && pos0 >= 0 && pos0 + 8 <= L)
+                q[u] = *reinterpret_cast<const uint4*>(rows + (size_t)c * L + pos0);
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = threadIdx.x + u * CF_THREADS;
+            if (e >= NITEM) break;
+            const int c = e & (CH - 1), v = e / CH;
+            const int pos0 = i0 - 8 + 8 * v;
             unsigned short t[8];
             if (pos0 >= 0 && pos0 + 8 <= L) {
-                const uint4 q = *reinterpret_cast<const uint4*>(src + pos0);
-                const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+                const uint32_t w[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     t[2 * k] = (unsigned short)(w[k] & 0xffffu);
                     t[2 * k + 1] = (unsigned short)(w[k] >> 16);
                 }
             } else {
+                const unsigned short* src = rows + (size_t)c * L;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) t[k] = (pos0 + k >= 0 && pos0 + k < L) ? src[pos0 + k] : 0;
             }
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int j = 8 * v - HALF + k;
-                if (j >= 0 && j < C5_XW) xs[c5_idx(j, c)] = t[k];
+                if (j >= 0 && j < C5_XW) xs[c5_idx<P>(j, c)] = t[k];
             }
         }
     } else {
@@ -475,36 +500,53 @@ __device__ __forceinline__ void c5_stage_act(const unsigned short* __restrict__ 
             const size_t o = (size_t)(2 * cp) * L + pos;
             const bool inside = pos >= 0 && pos < L;
             const uint32_t v0 = inside ? rows[o] : 0u, v1 = inside ? rows[o + L] : 0u;
-            *reinterpret_cast<uint32_t*>(xs + c5_idx(j, 2 * cp)) = v0 | (v1 << 16);
+            *reinterpret_cast<uint32_t*>(xs + c5_idx<P>(j, 2 * cp)) = v0 | (v1 << 16);
         }
     }
 }
 
-// The same from FP32 rows, split into BF16 hi (part 0) and lo (part 1).
+// The same from FP32 rows, split into BF16 hi (part 0) and lo (part 1); loads first, as above.
+template <int TPC>
 __device__ __forceinline__ void c5_stage_split(const float* __restrict__ rows, int L, int i0, unsigned short* xh,
                                                unsigned short* xl)
 {
-    for (int e = threadIdx.x; e < CH * (C5_XW / 4); e += blockDim.x) {
+    using G = C5<TPC>;
+    constexpr int C5_XW = G::XW, CF_THREADS = G::THREADS, P = G::PLANE;
+    constexpr int NITEM = CH * (C5_XW / 4), PER = (NITEM + CF_THREADS - 1) / CF_THREADS;
+    float4 q[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * CF_THREADS;
         const int c = e & (CH - 1), v = e / CH;
         const int pos0 = i0 - HALF + 4 * v;
         const float* src = rows + (size_t)c * L;
-        float t[4];
-        if ((L & 3) == 0 && pos0 >= 0 && pos0 + 4 <= L) {
-            const float4 q = *reinterpret_cast<const float4*>(src + pos0);
-            t[0] = q.x; t[1] = q.y; t[2] = q.z; t[3] = q.w;
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) t[k] = (pos0 + k >= 0 && pos0 + k < L) ? src[pos0 + k] : 0.f;
+        q[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < NITEM) {
+            if ((L & 3) == 0 && pos0 >= 0 && pos0 + 4 <= L) {
+                q[u] = *reinterpret_cast<const float4*>(src + pos0);
+            } else {
+                q[u].x = (pos0 >= 0 && pos0 < L) ? src[pos0] : 0.f;
+                q[u].y = (pos0 + 1 >= 0 && pos0 + 1 < L) ? src[pos0 + 1] : 0.f;
+                q[u].z = (pos0 + 2 >= 0 && pos0 + 2 < L) ? src[pos0 + 2] : 0.f;
+                q[u].w = (pos0 + 3 >= 0 && pos0 + 3 < L) ? src[pos0 + 3] : 0.f;
+            }
         }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * CF_THREADS;
+        if (e >= NITEM) break;
+        const int c = e & (CH - 1), v = e / CH;
+        const float t[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
 #pragma unroll
         for (int k = 0; k < 4; k += 2) {
             uint32_t hi, lo;
             isr::split2<true>(t[k], t[k + 1], hi, lo);
             const int j = 4 * v + k;
-            xh[c5_idx(j, c)] = (unsigned short)(hi & 0xffffu);
-            xh[c5_idx(j + 1, c)] = (unsigned short)(hi >> 16);
-            xl[c5_idx(j, c)] = (unsigned short)(lo & 0xffffu);
-            xl[c5_idx(j + 1, c)] = (unsigned short)(lo >> 16);
+            xh[c5_idx<P>(j, c)] = (unsigned short)(hi & 0xffffu);
+            xh[c5_idx<P>(j + 1, c)] = (unsigned short)(hi >> 16);
+            xl[c5_idx<P>(j, c)] = (unsigned short)(lo & 0xffffu);
+            xl[c5_idx<P>(j + 1, c)] = (unsigned short)(lo >> 16);
         }
     }
 }
@@ -512,14 +554,16 @@ __device__ __forceinline__ void c5_stage_split(const float* __restrict__ rows, i
 // FWD: in = BF16 activations [B][32][L], out = BF16 relu(conv + bias).
 // !FWD: in = FP32 gradient [B][32][L], out = FP32 conv masked by mask > 0, no bias.
 // wt: GEMM rows [out channel][tap][in channel] (BF16), as for conv_tc_kernel.
-template <bool FWD>
-__global__ void __launch_bounds__(CF_THREADS) conv_tc05_kernel(const void* __restrict__ in,
+template <bool FWD, int TPC>
+__global__ void __launch_bounds__(C5<TPC>::THREADS) conv_tc05_kernel(const void* __restrict__ in,
                                                                const __nv_bfloat16* __restrict__ wt,
                                                                const float* __restrict__ bias,
                                                                const __nv_bfloat16* __restrict__ mask, int L,
                                                                void* __restrict__ out)
 {
+    using G = C5<TPC>;
     constexpr int NX = FWD ? 1 : 2;
+    constexpr int C5_CT = G::CT, CF_THREADS = G::THREADS, C5_PART = G::PART, C5_PLANE = G::PLANE, C5_COLS = G::COLS;
     extern __shared__ __align__(128) unsigned char c5_smem[];
     unsigned char* xs = c5_smem;                                  // NX parts of 4 planes
     unsigned char* ws = c5_smem + NX * C5_PART;                   // 36 weight planes
@@ -532,15 +576,25 @@ __global__ void __launch_bounds__(CF_THREADS) conv_tc05_kernel(const void* __res
     if (warp == 0) isr::tmem_alloc(isr::smem_u32(tslot), C5_COLS);
     // weights: 16-byte piece (co, tap, 8-channel group g) of row co to plane (tap, g), row co
     const uint4* w4 = reinterpret_cast<const uint4*>(wt);
-    for (int e = tid; e < CH * KT * 4; e += CF_THREADS) {
+    constexpr int WPER = (CH * KT * 4 + CF_THREADS - 1) / CF_THREADS;
+    uint4 wq[WPER];
+#pragma unroll
+    for (int u = 0; u < WPER; ++u) {
+        const int e = tid + u * CF_THREADS;
+        if (e < CH * KT * 4) wq[u] = w4[e];
+    }
+#pragma unroll
+    for (int u = 0; u < WPER; ++u) {
+        const int e = tid + u * CF_THREADS;
+        if (e >= CH * KT * 4) break;
         const int co = e / (KT * 4), r = e - co * (KT * 4);      // r = tap * 4 + g
-        *reinterpret_cast<uint4*>(ws + (r * CH + co) * 16) = w4[e];
+        *reinterpret_cast<uint4*>(ws + (r * CH + co) * 16) = wq[u];
     }
     if constexpr (FWD)
-        c5_stage_act(static_cast<const unsigned short*>(in) + (size_t)b * CH * L, L, i0,
+        c5_stage_act<TPC>(static_cast<const unsigned short*>(in) + (size_t)b * CH * L, L, i0,
                      reinterpret_cast<unsigned short*>(xs));
     else
-        c5_stage_split(static_cast<const float*>(in) + (size_t)b * CH * L, L, i0, reinterpret_cast<unsigned short*>(xs),
+        c5_stage_split<TPC>(static_cast<const float*>(in) + (size_t)b * CH * L, L, i0, reinterpret_cast<unsigned short*>(xs),
                        reinterpret_cast<unsigned short*>(xs + C5_PART));
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the tiles, for the tensor cores
     isr::fence_barrier_init();
@@ -1217,10 +1271,10 @@ isr_status set_smem_attrs()
                                      (int)tc_smem_bytes(false)));
         EST_TRY(cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)wgrad_tc_smem_bytes()));
-        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)c5_smem_bytes(true)));
-        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)c5_smem_bytes(false)));
+        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<true, C5_TPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)C5<C5_TPC>::smem(true)));
+        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<false, C5_TPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)C5<C5_TPC>::smem(false)));
     }
     return ISR_OK;
 }
@@ -1247,7 +1301,8 @@ isr_status forward_t(isr_est* e, const float* x, int n, float* pos = nullptr, fl
         if constexpr (kTensorConv<T>) {
             const T* w = static_cast<const T*>(e->tf) + (size_t)(l - 2) * CH * CH * KT;
             if (e->conv05)
-                conv_tc05_kernel<true><<<dim3((L + C5_CT - 1) / C5_CT, n), CF_THREADS, c5_smem_bytes(true), s>>>(
+                conv_tc05_kernel<true, C5_TPC><<<dim3((L + C5<C5_TPC>::CT - 1) / C5<C5_TPC>::CT, n), C5<C5_TPC>::THREADS,
+                                                 C5<C5_TPC>::smem(true), s>>>(
                     act[l - 1], w, e->theta + b_off(l), nullptr, L, act[l]);
             else
                 conv_tc_kernel<true><<<dim3((L + CF_CT - 1) / CF_CT, n), CF_THREADS, tc_smem_bytes(true), s>>>(
@@ -1298,7 +1353,8 @@ isr_status backward_t(isr_est* e, int n, const float* fpos, const float* pres)
             if constexpr (kTensorConv<T>) {
                 const T* w = static_cast<const T*>(e->tb) + (size_t)(l - 2) * CH * CH * KT;
                 if (e->conv05)
-                    conv_tc05_kernel<false><<<dim3((L + C5_CT - 1) / C5_CT, n), CF_THREADS, c5_smem_bytes(false), s>>>(
+                    conv_tc05_kernel<false, C5_TPC><<<dim3((L + C5<C5_TPC>::CT - 1) / C5<C5_TPC>::CT, n),
+                                                      C5<C5_TPC>::THREADS, C5<C5_TPC>::smem(false), s>>>(
                         da, w, nullptr, act[l - 1], L, dn);
                 else
                     conv_tc_kernel<false><<<dim3((L + CF_CT - 1) / CF_CT, n), CF_THREADS, tc_smem_bytes(false), s>>>(

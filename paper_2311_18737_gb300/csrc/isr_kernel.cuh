@@ -783,9 +783,13 @@ struct SchedWL {
 // two pad elements per 32 keep even elements 16-byte aligned for paired stores
 __device__ __forceinline__ int pid32(int i) { return i + 2 * (i >> 5); }
 
-template <int LOG2N, int TXT, bool FULL, class A = const KArgs>
+// TMT: the first pass's twiddles W_N^{n q} and the last pass's W_1024^{l k} precomputed per thread
+// in tensor memory at tmem, and a thread's two first-pass columns n = t and t + T (instead of two
+// adjacent columns): the window reads become unit-stride (no bank conflicts) and the first-pass
+// outputs go out as single complex stores.
+template <int LOG2N, int TXT, bool FULL, class A = const KArgs, bool TMT = false>
 __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c, unsigned char* smem,
-                                                  const uint32_t phase0, const bool setup)
+                                                  const uint32_t phase0, const bool setup, const uint32_t tmem = 0)
 {
     using S = SchedWL<LOG2N>;
     constexpr int N = S::N, M = S::M, T = S::T, G = S::G, BF = S::BF;
@@ -812,17 +816,48 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
         const uint32_t* src = a.echo + (int64_t)p * a.echo_stride + (s_r - off);
         bulk_load(smem_u32(stage), src, copy_bytes, bar);
     };
+    // first-pass column of butterfly b of thread tt
+    auto col = [&](int tt, int b) { return TMT ? tt + T * b : 2 * (tt + T * (b >> 1)) + (b & 1); };
+    static_assert(!TMT || (G == 1 && (M - 1) * BF <= 32), "TMEM twiddles: one gate per CTA, <= 32 first-pass twiddles");
+    const uint32_t tw_tm = TMT ? tmem_warp_lane_base(tmem) + 128u * (uint32_t)(tid >> 7) : 0u;
 
     if (setup) __syncthreads();
-    for (int i = setup ? tid : 1024; i < 1024; i += kThreads) {   // bases W_N^n, slot [b][t]
+    if constexpr (TMT) {
+        if (setup) {
+            // columns [0, 64): first pass, entry b (M - 1) + i - 1 = W_N^{n bitrev(i)} for the
+            // register i that holds output bitrev(i); columns [64, 128): W_1024^{l k}, k = 1..31
+            static_for<8>([&](auto Cc) {
+                constexpr int cc = decltype(Cc)::value;
+                uint32_t rr[16];
+                static_for<8>([&](auto Ec) {
+                    constexpr int i8 = decltype(Ec)::value, e = 8 * (cc & 3) + i8;
+                    float sn = 0.f, cs = 0.f;
+                    if constexpr (cc < 4) {
+                        constexpr int b = e / (M - 1), i = e % (M - 1) + 1;
+                        if constexpr (b < BF) {
+                            const int n = col(t, b);
+                            sincospif(-2.f * (float)((n * BitRev<M>::at(i)) % N) / (float)N, &sn, &cs);
+                        }
+                    } else if constexpr (e < 31) {
+                        sincospif(-2.f * (float)((lane * (e + 1)) % 1024) / 1024.f, &sn, &cs);
+                    }
+                    rr[2 * i8] = __float_as_uint(cs);
+                    rr[2 * i8 + 1] = __float_as_uint(sn);
+                });
+                tmem_st16(tw_tm + 16u * cc, rr);
+            });
+            tmem_wait_st();
+        }
+    }
+    for (int i = (setup && !TMT) ? tid : 1024; i < 1024; i += kThreads) {   // bases W_N^n, slot [b][t]
         const int b = i / T, tt = i - b * T;
-        const int n = 2 * (tt + T * (b >> 1)) + (b & 1);
+        const int n = col(tt, b);
         float sn, cs;
         sincospif(-2.f * (float)n / (float)N, &sn, &cs);
         twb[i] = make_float2(cs, sn);
     }
     // three pairs per lane (w, w^2), (w^3, w^4), (w^8, w^16), w = W_1024^l (see twiddle_tab3)
-    for (int i = setup ? tid : 6 * 32; i < 6 * 32; i += kThreads) {
+    for (int i = (setup && !TMT) ? tid : 6 * 32; i < 6 * 32; i += kThreads) {
         const int e4 = i >> 1, pr = e4 / 32, l = e4 % 32;
         const int k = pr < 2 ? 2 * pr + 1 + (i & 1) : 8 << (i & 1);
         float sn, cs;
@@ -834,15 +869,14 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
 
     const char* txbase = reinterpret_cast<const char*>(a.tx);
     constexpr int CHIP = TXT == TX_CI16 ? 4 : TXT == TX_C32 ? 8 : 1;
-    // first-pass chips of this thread: bit b M + k for position n + 1024 k,
-    // n = 2 (t + T (b / 2)) + b % 2
+    // first-pass chips of this thread: bit b M + k for position col(t, b) + 1024 k
     auto signs_of = [&](const int8_t* row) {
         uint32_t m = 0;
         static_for<BF>([&](auto Bc) {
             constexpr int b = decltype(Bc)::value;
             static_for<M>([&](auto Kc) {
                 constexpr int k = decltype(Kc)::value;
-                const int pos = 2 * (t + T * (b >> 1)) + (b & 1) + 1024 * k;
+                const int pos = col(t, b) + 1024 * k;
                 if (pos < a.code_len && row[pos] < 0) m |= 1u << (b * M + k);
             });
         });
@@ -875,7 +909,7 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
         float2 zp[M] = {};   // even butterflies fill it before the odd ones read it
         static_for<BF>([&](auto Bc) {
             constexpr int b = decltype(Bc)::value;
-            const int n = 2 * (t + T * (b >> 1)) + (b & 1);
+            const int n = col(t, b);
             float2 u[M];
             static_for<M>([&](auto Kc) {
                 constexpr int k = decltype(Kc)::value;
@@ -885,6 +919,14 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
                     u[k] = decode<TXT>(stage[off + pos], txrow, pos, (signs << (31 - (b * M + k))) & 0x80000000u);
             });
             sdft<M>(u);
+            if constexpr (TMT) {
+                twiddle_tmem<M, b>(u, tw_tm);   // u[i] *= W_N^{n bitrev(i)}
+                static_for<M>([&](auto Qc) {
+                    constexpr int q = decltype(Qc)::value;
+                    reg[q * S::RPAD + pid32(n)] = u[BitRev<M>::at(q)];
+                });
+                return;
+            }
             const float2 w = twb[b * T + t];
             float2 cur = w;
             static_for<M>([&](auto Qc) {
@@ -926,7 +968,8 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
             constexpr int k = decltype(Kc)::value;
             v[k] = rw[lane + 34 * k];
         });
-        twiddle_tab3<32, 32>(v, tabc, lane);
+        if constexpr (TMT) twiddle_tmem<32, 0>(v, tw_tm + 64u);
+        else twiddle_tab3<32, 32>(v, tabc, lane);
         sdft<32>(v);
         static_for<32>([&](auto Qc) {
             constexpr int q = decltype(Qc)::value;
@@ -946,6 +989,28 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
         for (int q = 0; q < 32; ++q) out[wg + M * (lane + 32 * q)] = acc[q];
     }
     return true;
+}
+
+// The warp-local schedule with its twiddles in tensor memory (512 columns, one CTA per SM).
+template <int LOG2N, int TXT, bool FULL>
+__global__ void __launch_bounds__(kThreads, 1) integrate_kernel_wl_tm(KArgs a)
+{
+    using S = SchedWL<LOG2N>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MBAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::OFF_MBAR + 8 * 7);
+    if (threadIdx.x < S::G) mbar_init(smem_u32(&mbar[threadIdx.x]), 1);
+    if (threadIdx.x < 32) tmem_alloc(smem_u32(tslot), 512);
+    fence_barrier_init();
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    const uint32_t tbase = *tslot;
+    integrate_unit_wl<LOG2N, TXT, FULL, const KArgs, true>(a, blockIdx.x, blockIdx.y, smem, 0u, true, tbase);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (threadIdx.x < 32) tmem_dealloc(tbase, 512);
 }
 
 template <int LOG2N, int TXT, bool FULL>

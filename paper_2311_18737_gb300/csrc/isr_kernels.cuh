@@ -12,8 +12,8 @@ isr_status fail(isr_status st, const char* fmt, ...);
 void clear_error();
 
 // radix orders: 0-2 Stockham, 3 warp-local, 4-5 paired FP32, 6-8 orders 0-2 with the inter-pass
-// twiddles in tensor memory
-constexpr int kNumOrders = 9;
+// twiddles in tensor memory, 9 the warp-local schedule with its twiddles in tensor memory
+constexpr int kNumOrders = 10;
 
 struct KernelEntry {
     const void* fn;   // __global__ integrate_kernel<LOG2N, TXT>
@@ -36,8 +36,8 @@ KernelEntry entry_for(int txt)
                   : txt == TX_C32  ? (const void*)integrate_kernel<L, TX_C32>
                                    : (const void*)integrate_kernel<L, TX_PM1>;
     const void* ff = txt == TX_PM1 ? (const void*)integrate_kernel<L, TX_PM1, true> : f;
-    KernelEntry e{f, ff, {ff, ff, ff, ff, ff, ff, ff, ff, ff},
-                  {S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM},
+    KernelEntry e{f, ff, {ff, ff, ff, ff, ff, ff, ff, ff, ff, ff},
+                  {S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM, S::SMEM},
                   {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
                   0, S::SMEM, S::G, kThreads};
     if constexpr (L >= 11) {
@@ -62,6 +62,8 @@ KernelEntry entry_for(int txt)
             e.smem_order[7] = Sched<14, 1, true>::SMEM;
             e.fn_order[8] = (const void*)integrate_kernel_tm<14, TX_PM1, true, 2>;
             e.smem_order[8] = Sched<14, 2, true>::SMEM;
+            e.fn_order[9] = (const void*)integrate_kernel_wl_tm<14, TX_PM1, true>;
+            e.smem_order[9] = SchedWL<14>::SMEM;
             e.fn_tc[1] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_BF16_SPLIT>;
             e.fn_tc[2] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_FP16_SPLIT>;
             e.fn_tc[3] = (const void*)integrate_kernel<14, TX_PM1, true, 1, P0_BF16>;

@@ -41,7 +41,7 @@ EXPORTS = ("isr_plan_create", "isr_integrate", "isr_spectra", "isr_plan_query", 
            "isr_batch_create", "isr_batch_run", "isr_batch_wait", "isr_batch_query", "isr_batch_destroy")
 
 # radix orders of isr_plan_set_order (4..8 at nfft 16384 with binary-phase codes only)
-N_ORDERS = 9
+N_ORDERS = 10
 
 ISR_PREC_FP32 = 0
 ISR_PREC_TC_BF16_SPLIT = 1

@@ -237,7 +237,7 @@ def test_timeout_is_reported_and_context_survives(nfft):
     _timeout_case(nfft, 0)
 
 
-@pytest.mark.parametrize("order", [3, 6, 7])
+@pytest.mark.parametrize("order", [3, 6, 7, 9])
 def test_timeout_every_barrier_kind_at_16384(order):
     # warp-local schedule (CTA + warp barriers) and tensor-memory twiddles (the CTA frees its
     # TMEM on the timeout path)
