@@ -289,7 +289,11 @@ def run_ours(args):
     plan = isr.Plan(nfft=N, n_ranges=R, echo_stride=echo_stride, range_start=range_start,
                     range_step=w.range_step, tx_type=isr.ISR_TX_PM1, device=local, stream=stream)
     # radix order: time the candidates on a probe of the workload and keep the fastest
-    if args.order is not None:
+    if args.precision:
+        # a tensor-core first-pass engine (nfft 16384, radix order 1): a precision-study run
+        isr.isr_plan_set_precision(plan.handle, args.precision)
+        tune = {"order": 1, "ms": []}
+    elif args.order is not None:
         isr.isr_plan_set_order(plan.handle, args.order)
         tune = {"order": args.order, "ms": []}
     elif args.no_autotune:
@@ -391,7 +395,8 @@ def run_ours(args):
                                                            "blocks gathered to rank 0 each step") if strong else
                        "independent problem per rank", "l2": "inputs larger than L2 (echo %.2f GB per step)" % (
                            echo.numel() * 2 / 1e9), "kernel": "fused decode+FFT+|X|^2, chunks of %d IPPs" %
-                       plan.info()["ipp_chunk"], "radix_order": tune["order"], "radix_order_probe_ms": tune["ms"],
+                       plan.info()["ipp_chunk"], "first_pass_engine": isr.PRECISION_NAMES[args.precision],
+                       "radix_order": tune["order"], "radix_order_probe_ms": tune["ms"],
                        "realtime_factor_at_10ms_ipp": (P * 0.010) / (ms / 1000)},
             "gpu_launches": gpu_launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
@@ -461,6 +466,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--order", type=int, default=None, help="force a radix order (no autotuning)")
     ap.add_argument("--no-peak", action="store_true", help="skip the FP32 FMA-rate microkernel")
+    ap.add_argument("--precision", type=int, default=0,
+                    help="first-pass engine (isr_plan_set_precision): 0 SIMT FP32; 1-4 mma.sync, 5-8 tcgen05 tensor cores")
     ap.add_argument("--ref-gates", type=int, default=256)
     ap.add_argument("--ref-ipps", type=int, default=256)
     ap.add_argument("--n-ranges", type=int, default=None, help="resize the workload (profiling cases)")
