@@ -769,6 +769,155 @@ __global__ void __launch_bounds__(256, 4) wgrad_tc_kernel(const __nv_bfloat16* _
     if (tid < CH) atomicAdd(&db[tid], db_s[tid]);
 }
 
+// Weight gradient of layers 2-4 on tcgen05 (ISR_EST_BF16):
+//   dW[co][ci][k] = sum_p da[co][p] h[ci][p + k - 4]   over the CTA's span of one row,
+// as D[row][32 k + ci] = sum_p A[row][p] B_k[ci][p] with K = positions (16 per MMA), rows 0-31 the
+// BF16 hi parts of da and rows 32-63 its lo parts (their sum keeps ~16 bits of the FP32
+// gradient), N = 32 per tap (TMEM columns 32 k, 288 in all).  In the no-swizzle layouts of both
+// majors the descriptor's leading-byte offset steps along K and its stride-byte offset along
+// M or N.  A is K-major: 8 x 8 blocks
+// [8 channels][8 positions] staged straight from the channel-major rows; rows 64-127 of the
+// M = 128 instruction read whatever lies beyond the real rows (the next staging buffer or the
+// activation tiles) and land in accumulator rows that are never read.  B_k is the activation tile
+// in its position-major planes (MN-major: 8 channels per 16-byte row, positions as rows), started
+// k rows later for tap k.  Chunks of 256 positions are double-buffered: while the tensor core
+// runs one chunk's 144 MMAs, the CTA stages the next.  One CTA per SM (512 TMEM columns).
+constexpr int W5_CHUNK = 256;                    // positions per chunk (16 K-steps)
+constexpr int W5_THREADS = 256;
+constexpr int W5_ASBO = W5_CHUNK / 8 * 128;      // bytes per 8-row group of A (all its 8-position blocks)
+constexpr int W5_ABUF = 8 * W5_ASBO;             // one A buffer: 8 real row groups (hi 0-3, lo 4-7)
+using W5X = C5<2>;                               // activation tile: 256 + 8 rows, 4 planes
+static_assert(W5X::CT == W5_CHUNK && W5X::THREADS == W5_THREADS, "activation tile matches the chunk");
+constexpr size_t w5_smem_bytes() { return (size_t)2 * W5_ABUF + 2 * W5X::PART + 64; }
+// dynamic shared memory requested at launch: more than half an SM's, so that one CTA (and its 512
+// TMEM columns) has the SM to itself and no second CTA waits in tcgen05.alloc
+constexpr size_t W5_SMEM_LAUNCH = 120 * 1024;
+static_assert(w5_smem_bytes() <= W5_SMEM_LAUNCH, "launch request covers the layout");
+// rows 64-127 of either A buffer stay inside the allocation
+static_assert((size_t)W5_ABUF + 16 * W5_ASBO <= 2 * W5_ABUF + 2 * W5X::PART, "A's unused rows stay in shared memory");
+
+__global__ void __launch_bounds__(W5_THREADS, 1) wgrad_tc05_kernel(const __nv_bfloat16* __restrict__ h,
+                                                                   const float* __restrict__ da, int L, int span,
+                                                                   float* __restrict__ dW, float* __restrict__ db)
+{
+    extern __shared__ __align__(128) unsigned char w5_smem[];
+    unsigned char* abuf = w5_smem;                                  // [2][8 row groups][W5_ASBO]
+    unsigned char* xbuf = w5_smem + 2 * W5_ABUF;                    // [2][W5X::PART]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(w5_smem + 2 * W5_ABUF + 2 * W5X::PART);   // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    __shared__ float db_s[CH];
+    const int b = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int p_begin = blockIdx.x * span, span_end = min(L, p_begin + span);
+    const int nch = (span_end - p_begin + W5_CHUNK - 1) / W5_CHUNK;
+    if (tid < CH) db_s[tid] = 0.f;
+    if (tid == 0) {
+        isr::mbar_init(isr::smem_u32(&mbar[0]), 1);
+        isr::mbar_init(isr::smem_u32(&mbar[1]), 1);
+    }
+    if (warp == 0) isr::tmem_alloc(isr::smem_u32(tslot), 512);
+
+    // stage chunk c into buffer c & 1: da as hi / lo 8 x 8 blocks, the activations as planes
+    auto stage = [&](int c) {
+        const int p0 = p_begin + c * W5_CHUNK;
+        unsigned char* a = abuf + (c & 1) * W5_ABUF;
+        constexpr int NITEM = CH * (W5_CHUNK / 8), PER = NITEM / W5_THREADS;   // (channel, 8-position block)
+        float4 q0[PER], q1[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = tid + u * W5_THREADS;
+            const int co = e / (W5_CHUNK / 8), kb = e - co * (W5_CHUNK / 8);
+            const int pos = p0 + 8 * kb;
+            const float* src = da + ((size_t)b * CH + co) * L + pos;
+            if ((L & 3) == 0 && pos + 8 <= span_end) {
+                q0[u] = *reinterpret_cast<const float4*>(src);
+                q1[u] = *reinterpret_cast<const float4*>(src + 4);
+            } else {
+                float t[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) t[k] = pos + k < span_end ? src[k] : 0.f;
+                q0[u] = make_float4(t[0], t[1], t[2], t[3]);
+                q1[u] = make_float4(t[4], t[5], t[6], t[7]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = tid + u * W5_THREADS;
+            const int co = e / (W5_CHUNK / 8), kb = e - co * (W5_CHUNK / 8);
+            const float t[8] = {q0[u].x, q0[u].y, q0[u].z, q0[u].w, q1[u].x, q1[u].y, q1[u].z, q1[u].w};
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) isr::split2<true>(t[2 * k], t[2 * k + 1], hi[k], lo[k]);
+            const uint32_t o = (uint32_t)((co >> 3) * W5_ASBO + kb * 128 + (co & 7) * 16);
+            *reinterpret_cast<uint4*>(a + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(a + o + 4 * W5_ASBO) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            // bias gradient: the lanes of a warp share the channel
+            float sum = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+            for (int off = 16; off; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off);
+            if (lane == 0) atomicAdd(&db_s[co], sum);
+        }
+        c5_stage_act<2>(reinterpret_cast<const unsigned short*>(h) + (size_t)b * CH * L, L, p0,
+                        reinterpret_cast<unsigned short*>(xbuf + (c & 1) * W5X::PART));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    };
+
+    if (nch > 0) stage(0);
+    isr::fence_barrier_init();
+    isr::tmem_fence_before_sync();
+    __syncthreads();
+    isr::tmem_fence_after_sync();
+    const uint32_t tbase = *tslot;
+    // A K-major (bit 15 = 0), B MN-major (bit 16 = 1)
+    constexpr uint32_t idesc = isr::tc05_idesc<true>() | (1u << 16);
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+        if (tid == 0) {
+            isr::tmem_fence_after_sync();
+            const uint32_t aa = isr::smem_u32(abuf + (c & 1) * W5_ABUF);
+            const uint32_t xa = isr::smem_u32(xbuf + (c & 1) * W5X::PART);
+#pragma unroll 1
+            for (int s = 0; s < W5_CHUNK / 16; ++s) {
+                const uint64_t ad = isr::tc05_desc(aa + s * 256, 128, W5_ASBO);           // LBO: K, SBO: rows (M)
+#pragma unroll 1
+                for (int tap = 0; tap < KT; ++tap) {
+                    // no swizzle: LBO steps along K (8 positions = 128 B), SBO along N (8 channels = a plane)
+                    const uint64_t bd = isr::tc05_desc(xa + (16 * s + tap) * 16, 128, W5X::PLANE);
+                    isr::tc05_mma(tbase + 32u * tap, ad, bd, idesc, (c > 0 || s > 0) ? 1u : 0u);
+                }
+            }
+            isr::tc05_commit(isr::smem_u32(&mbar[c & 1]));
+        }
+        if (c + 1 < nch) {
+            // the buffer of chunk c + 1 was read by chunk c - 1's MMAs
+            if (c >= 1) ok = isr::mbar_wait(isr::smem_u32(&mbar[(c + 1) & 1]), (uint32_t)((c - 1) >> 1) & 1u, 1u << 26) && ok;
+            stage(c + 1);
+        }
+        isr::tmem_fence_before_sync();
+        __syncthreads();
+    }
+    // the last commit covers every MMA of this CTA
+    if (nch > 0) ok = isr::mbar_wait(isr::smem_u32(&mbar[(nch - 1) & 1]), (uint32_t)((nch - 1) >> 1) & 1u, 1u << 26) && ok;
+    isr::tmem_fence_after_sync();
+    // epilogue: rows 0-31 (hi, lane quarter 0) and 32-63 (lo, quarter 1); warps 0-1 taps 0-4,
+    // warps 4-5 taps 5-8
+    const int quarter = warp & 3, half = warp >> 2;
+    if (nch > 0 && ok && quarter < 2) {
+        const int co = lane;
+#pragma unroll 1
+        for (int tap = half * 5; tap < (half ? KT : 5); ++tap) {
+            uint32_t r[32];
+            isr::tmem_ld32(isr::tmem_warp_lane_base(tbase) + 32u * tap, r);
+            isr::tmem_wait_ld32(r);
+#pragma unroll
+            for (int ci = 0; ci < CH; ++ci) atomicAdd(&dW[((size_t)co * CH + ci) * KT + tap], __uint_as_float(r[ci]));
+        }
+    }
+    isr::tmem_fence_before_sync();
+    __syncthreads();
+    isr::tmem_fence_after_sync();
+    if (warp == 0) isr::tmem_dealloc(tbase, 512);
+    if (tid < CH) atomicAdd(&db[tid], db_s[tid]);
+}
+
 // dW[co][ci][k] += sum_i da[b][co][i] h[b][ci][i + k - 4];  db[co] += sum_i da[b][co][i]
 // CTA: one row b, positions [i0, i0 + WG_SPAN); lane = co, warp = group of CIN/8 input channels
 constexpr int WG_SPAN = 1152;
@@ -1228,6 +1377,7 @@ struct isr_est {
     bool weights_stale = true;                // the working weights need the master copy's values
     int wgrad_slots = 0;                      // resident tensor-core weight-gradient CTAs (all SMs)
     bool conv05 = false;                      // BF16 convolutions on tcgen05 (else mma.sync)
+    int sms = 0;                              // multiprocessors of the device
     int* pidx = nullptr;
     float *da0 = nullptr, *da1 = nullptr; // gradient ping-pong [B][32][L]
 };
@@ -1271,6 +1421,8 @@ isr_status set_smem_attrs()
                                      (int)tc_smem_bytes(false)));
         EST_TRY(cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)wgrad_tc_smem_bytes()));
+        EST_TRY(cudaFuncSetAttribute(wgrad_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)W5_SMEM_LAUNCH));
         EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<true, C5_TPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)C5<C5_TPC>::smem(true)));
         EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<false, C5_TPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1344,10 +1496,17 @@ isr_status backward_t(isr_est* e, int n, const float* fpos, const float* pres)
         if (l == 1) {
             wgrad_kernel<T, 1><<<gw, 256, 0, s>>>(act[0], da, L, e->grad + OFF_W1, e->grad + OFF_B1);
         } else {
-            if constexpr (kTensorConv<T>)
-                wgrad_tc_kernel<<<dim3((L + span - 1) / span, n), 256, wgrad_tc_smem_bytes(), s>>>(
-                    act[l - 1], da, L, span, e->grad + w_off(l), e->grad + b_off(l));
-            else
+            if constexpr (kTensorConv<T>) {
+                if (e->conv05) {
+                    const int span5 = W5_CHUNK * wgrad_span_chunks(L, n, e->sms);
+                    wgrad_tc05_kernel<<<dim3((L + span5 - 1) / span5, n), W5_THREADS, W5_SMEM_LAUNCH, s>>>(
+                        reinterpret_cast<const __nv_bfloat16*>(act[l - 1]), da, L, span5, e->grad + w_off(l),
+                        e->grad + b_off(l));
+                } else {
+                    wgrad_tc_kernel<<<dim3((L + span - 1) / span, n), 256, wgrad_tc_smem_bytes(), s>>>(
+                        act[l - 1], da, L, span, e->grad + w_off(l), e->grad + b_off(l));
+                }
+            } else
                 wgrad_kernel<T, CH><<<gw, 256, 0, s>>>(act[l - 1], da, L, e->grad + w_off(l), e->grad + b_off(l));
             // gradient into the layer below, masked by its ReLU: da_{l-1} = (W_l^T * da_l) (h_{l-1} > 0)
             if constexpr (kTensorConv<T>) {
@@ -1464,6 +1623,7 @@ isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t 
             if (r == cudaSuccess)
                 r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wgrad_tc_kernel, 256, wgrad_tc_smem_bytes());
             e->wgrad_slots = std::max(1, occ) * std::max(1, sms);
+            e->sms = std::max(1, sms);
         }
     }
     if (r != cudaSuccess) {

@@ -92,8 +92,8 @@ def _dyadic_case(B=4, L=600, seed=7, precision=isr.ISR_EST_BF16):
     theta = ref.pack(d).astype(np.float32)
     x = (rng.integers(-8, 9, (B, L)) / 4.0).astype(np.float32)
     f = rng.uniform(3, L - 3, B).astype(np.float32)
-    y = np.array([1, 0, 1, 1][:B], dtype=np.float32)
-    e = est_mod.Estimator(max_batch=8, precision=precision, nfft=2048, band_lo=0, band_len=L)
+    y = np.resize(np.array([1, 0, 1, 1], dtype=np.float32), B)
+    e = est_mod.Estimator(max_batch=max(8, B), precision=precision, nfft=2048, band_lo=0, band_len=L)
     e.set_params(theta)
     dev = torch.device("cuda:0")
     return e, theta, x, f, y, [torch.from_numpy(a).to(dev) for a in (x, f, y)]
@@ -168,4 +168,23 @@ def test_training_gains_over_peak_fit():
     print(res)
     assert res["presence_accuracy"]["network"] >= res["presence_accuracy"]["peak_fit"]
     assert res["agreement_with_peak_fit_above_-10dB"] >= 0.9
+    e.close()
+
+
+@pytest.mark.parametrize("precision", ENGINES)
+def test_bf16_gradients_many_rows_several_chunks_per_cta(precision):
+    """64 rows x 1100 positions: the tcgen05 weight gradient then runs 768-position spans, three
+    256-position chunks per CTA through its double-buffered staging (two in the row's last CTA),
+    and the tcgen05 convolutions run three 256-position CTAs per row; exact (dyadic) inputs, the
+    same bound as the other BF16 gradient tests."""
+    e, theta, x, f, y, (xd, fd, yd) = _dyadic_case(B=64, L=1100, seed=9, precision=precision)
+    loss, g = e.grad(xd, fd, yd)
+    rl, rg = ref.loss_and_grad(theta.astype(np.float64), x, f, y, store=ref.round_bf16)
+    assert abs(loss - rl) <= 1e-4 * abs(rl)
+    gd, rd = ref.unpack(g.astype(np.float64)), ref.unpack(rg)
+    gmax = np.abs(rg).max()
+    for name, _ in ref.SHAPES:
+        scale = max(np.abs(rd[name]).max(), 1e-3 * gmax)
+        err = np.abs(gd[name] - rd[name]).max() / scale
+        assert err <= 1e-3, f"{name}: max error {err:.2e} of the block's largest gradient"
     e.close()
