@@ -248,18 +248,17 @@ isr_status isr_fp32_peak(int32_t device, int32_t paired, double* tflops, double*
  * and mean; parameters as a flat float vector of ISR_EST_N_PARAMS in the order
  * W1[32][1][9] b1[32] W2[32][32][9] b2 W3 b3 W4 b4 w5[32] b5[1] Wa[32][64] ba[32] wb[32] bb[1].
  * Training keeps FP32 master weights and Adam moments; activations and working weights
- * use `precision` (ISR_EST_FP32, ISR_EST_BF16 or ISR_EST_BF16_MMASYNC) with FP32 accumulation.
+ * use `precision` (ISR_EST_FP32 or one of the BF16 values below) with FP32 accumulation.
  * With BF16 storage the 32-channel convolutions (forward, backward-data, weight gradient) run
- * on the tensor cores: forward and backward-data as tcgen05.mma GEMMs with positions as M (one
- * thread issues them, the accumulators live in tensor memory) for ISR_EST_BF16, as warp-level
- * mma.sync for ISR_EST_BF16_MMASYNC; the weight gradient on mma.sync in both;
+ * on the tensor cores, as tcgen05.mma GEMMs (one thread issues them, the accumulators live in
+ * tensor memory) or as warp-level mma.sync, per the constants below;
  * the FP32 gradient entering the backward passes is split into two BF16 parts (~16
  * significant bits) for them.  All array arguments are device memory except where noted;
  * calls are ordered on `stream`.
  */
 #define ISR_EST_N_PARAMS 30210
 #define ISR_EST_FP32 0
-#define ISR_EST_BF16 1         /* BF16 storage, 32-channel convolutions on tcgen05 (TMEM accumulators) */
+#define ISR_EST_BF16 1         /* BF16 storage, the 32-channel convolutions on tcgen05 (TMEM accumulators) */
 #define ISR_EST_BF16_MMASYNC 2 /* BF16 storage, the same convolutions on the warp-level mma.sync path */
 typedef struct isr_est isr_est;
 

@@ -564,6 +564,7 @@ __global__ void __launch_bounds__(C5<TPC>::THREADS) conv_tc05_kernel(const void*
     using G = C5<TPC>;
     constexpr int NX = FWD ? 1 : 2;
     constexpr int C5_CT = G::CT, CF_THREADS = G::THREADS, C5_PART = G::PART, C5_PLANE = G::PLANE, C5_COLS = G::COLS;
+    static_assert(C5_PLANE % 16 == 0 && C5_PART % 16 == 0, "descriptor steps are whole 16-byte units");
     extern __shared__ __align__(128) unsigned char c5_smem[];
     unsigned char* xs = c5_smem;                                  // NX parts of 4 planes
     unsigned char* ws = c5_smem + NX * C5_PART;                   // 36 weight planes
@@ -605,23 +606,27 @@ __global__ void __launch_bounds__(C5<TPC>::THREADS) conv_tc05_kernel(const void*
 
     if (tid == 0) {
         constexpr uint32_t idesc = isr::tc05_idesc<true>();      // BF16, FP32 accumulate, M 128, N 32
-        const uint32_t xa = isr::smem_u32(xs), wa = isr::smem_u32(ws);
+        // descriptors built once and stepped in 16-byte units of the start field (addresses stay
+        // below 0x40000 B, so the 14-bit field never carries): tap k starts the A tile k rows
+        // (16 B each) later and B at weight plane 4 k; K-step ks moves A by two channel planes
+        // and B by two weight planes (512 B each)
+        const uint64_t bd0 = isr::tc05_desc(isr::smem_u32(ws), 512, 128);
 #pragma unroll 1
         for (int m = 0; m < C5_CT / 128; ++m) {
             uint32_t acc = 0;
 #pragma unroll 1
-            for (int part = 0; part < NX; ++part)
-#pragma unroll 1
+            for (int part = 0; part < NX; ++part) {
+                // rows 128 m + tap of the tile, channels 16 ks .. (planes 2 ks, 2 ks + 1)
+                const uint64_t ad0 = isr::tc05_desc(isr::smem_u32(xs) + part * C5_PART + 128 * m * 16, C5_PLANE, 128);
+#pragma unroll
                 for (int tap = 0; tap < KT; ++tap)
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
-                        // rows 128 m + tap of the tile, channels 16 ks .. (planes 2 ks, 2 ks + 1)
-                        const uint64_t ad = isr::tc05_desc(xa + part * C5_PART + 2 * ks * C5_PLANE + (128 * m + tap) * 16,
-                                                           C5_PLANE, 128);
-                        const uint64_t bd = isr::tc05_desc(wa + (tap * 4 + 2 * ks) * 512, 512, 128);
-                        isr::tc05_mma(tbase + 32u * m, ad, bd, idesc, acc);
+                        isr::tc05_mma(tbase + 32u * m, ad0 + (uint32_t)(tap + ks * (2 * C5_PLANE / 16)),
+                                      bd0 + (uint32_t)((tap * 4 + 2 * ks) * (512 / 16)), idesc, acc);
                         acc = 1;
                     }
+            }
         }
         isr::tc05_commit(isr::smem_u32(mbar));
     }
@@ -820,12 +825,14 @@ __global__ void __launch_bounds__(W5_THREADS, 1) wgrad_tc05_kernel(const __nv_bf
     auto stage = [&](int c) {
         const int p0 = p_begin + c * W5_CHUNK;
         unsigned char* a = abuf + (c & 1) * W5_ABUF;
-        constexpr int NITEM = CH * (W5_CHUNK / 8), PER = NITEM / W5_THREADS;   // (channel, 8-position block)
+        // items (8-position block kb, channel co) with the channel fastest: the eight lanes of a
+        // 16-byte store phase write one 128-byte core matrix (no bank conflicts)
+        constexpr int NITEM = CH * (W5_CHUNK / 8), PER = NITEM / W5_THREADS;
         float4 q0[PER], q1[PER];
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int e = tid + u * W5_THREADS;
-            const int co = e / (W5_CHUNK / 8), kb = e - co * (W5_CHUNK / 8);
+            const int co = e & (CH - 1), kb = e / CH;
             const int pos = p0 + 8 * kb;
             const float* src = da + ((size_t)b * CH + co) * L + pos;
             if ((L & 3) == 0 && pos + 8 <= span_end) {
@@ -842,7 +849,7 @@ __global__ void __launch_bounds__(W5_THREADS, 1) wgrad_tc05_kernel(const __nv_bf
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int e = tid + u * W5_THREADS;
-            const int co = e / (W5_CHUNK / 8), kb = e - co * (W5_CHUNK / 8);
+            const int co = e & (CH - 1), kb = e / CH;
             const float t[8] = {q0[u].x, q0[u].y, q0[u].z, q0[u].w, q1[u].x, q1[u].y, q1[u].z, q1[u].w};
             uint32_t hi[4], lo[4];
 #pragma unroll
@@ -850,10 +857,8 @@ __global__ void __launch_bounds__(W5_THREADS, 1) wgrad_tc05_kernel(const __nv_bf
             const uint32_t o = (uint32_t)((co >> 3) * W5_ASBO + kb * 128 + (co & 7) * 16);
             *reinterpret_cast<uint4*>(a + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
             *reinterpret_cast<uint4*>(a + o + 4 * W5_ASBO) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-            // bias gradient: the lanes of a warp share the channel
-            float sum = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
-            for (int off = 16; off; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off);
-            if (lane == 0) atomicAdd(&db_s[co], sum);
+            // bias gradient (lane = channel: 32 distinct shared addresses per warp)
+            atomicAdd(&db_s[co], ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7])));
         }
         c5_stage_act<2>(reinterpret_cast<const unsigned short*>(h) + (size_t)b * CH * L, L, p0,
                         reinterpret_cast<unsigned short*>(xbuf + (c & 1) * W5X::PART));
@@ -872,17 +877,19 @@ __global__ void __launch_bounds__(W5_THREADS, 1) wgrad_tc05_kernel(const __nv_bf
     for (int c = 0; c < nch; ++c) {
         if (tid == 0) {
             isr::tmem_fence_after_sync();
-            const uint32_t aa = isr::smem_u32(abuf + (c & 1) * W5_ABUF);
-            const uint32_t xa = isr::smem_u32(xbuf + (c & 1) * W5X::PART);
+            // no swizzle: A's LBO steps along K (8 positions = 128 B) and its SBO along M (8 rows);
+            // B's LBO along K (8 positions = 128 B) and its SBO along N (8 channels = a plane).  The
+            // descriptors are built once: the start field counts 16-byte units, so K-step s adds
+            // 16 (256 B) to both and tap k adds k (one 16-byte row) to B.  Every address stays in
+            // the shared window (below 0x40000 B), so the 14-bit field never carries.
+            const uint64_t ad0 = isr::tc05_desc(isr::smem_u32(abuf + (c & 1) * W5_ABUF), 128, W5_ASBO);
+            const uint64_t bd0 = isr::tc05_desc(isr::smem_u32(xbuf + (c & 1) * W5X::PART), 128, W5X::PLANE);
 #pragma unroll 1
             for (int s = 0; s < W5_CHUNK / 16; ++s) {
-                const uint64_t ad = isr::tc05_desc(aa + s * 256, 128, W5_ASBO);           // LBO: K, SBO: rows (M)
-#pragma unroll 1
-                for (int tap = 0; tap < KT; ++tap) {
-                    // no swizzle: LBO steps along K (8 positions = 128 B), SBO along N (8 channels = a plane)
-                    const uint64_t bd = isr::tc05_desc(xa + (16 * s + tap) * 16, 128, W5X::PLANE);
-                    isr::tc05_mma(tbase + 32u * tap, ad, bd, idesc, (c > 0 || s > 0) ? 1u : 0u);
-                }
+                const uint64_t ad = ad0 + 16u * (uint32_t)s, bd = bd0 + 16u * (uint32_t)s;
+                const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
+#pragma unroll
+                for (int tap = 0; tap < KT; ++tap) isr::tc05_mma(tbase + 32u * tap, ad, bd + (uint32_t)tap, idesc, acc);
             }
             isr::tc05_commit(isr::smem_u32(&mbar[c & 1]));
         }

@@ -12,6 +12,10 @@ from paper_2311_18737_gb300 import isr
 
 pytestmark = pytest.mark.gpu
 
+# Both BF16 engines: tcgen05 (convolutions in 256-position CTAs of two M = 128 tiles, the weight
+# gradient in 256-position chunks) and mma.sync.
+ENGINES = [isr.ISR_EST_BF16, isr.ISR_EST_BF16_MMASYNC]
+
 
 def _setup(precision, B=4, L=256, seed=0):
     rng = np.random.default_rng(seed)
@@ -52,7 +56,7 @@ def test_bf16_storage_close_to_reference():
     e.close()
 
 
-@pytest.mark.parametrize("precision", [isr.ISR_EST_BF16, isr.ISR_EST_BF16_MMASYNC])
+@pytest.mark.parametrize("precision", ENGINES)
 def test_bf16_gradients_per_block_against_rounding_reference(precision):
     """Random inputs (not dyadic): the BF16 variant against the FP64 reference that rounds to
     BF16 exactly where the variant stores (input, conv weights, activations).  What is left is
@@ -99,13 +103,9 @@ def _dyadic_case(B=4, L=600, seed=7, precision=isr.ISR_EST_BF16):
     return e, theta, x, f, y, [torch.from_numpy(a).to(dev) for a in (x, f, y)]
 
 
-# Both BF16 convolution engines: tcgen05 (512-position CTAs of four M = 128 tiles) and mma.sync
-# (256/512-position tiles).  600: full tiles and a ragged rest; 37: odd (unpaired stores), one
-# partial tile; 1100: three tcgen05 CTAs with a length that is not a multiple of 8 (the
+# Lengths: 600 spans full tiles and a ragged rest; 37 is odd (unpaired stores), one partial
+# tile; 1100 gives three tcgen05 CTAs with a length that is not a multiple of 8 (the
 # word-by-word staging path).
-ENGINES = [isr.ISR_EST_BF16, isr.ISR_EST_BF16_MMASYNC]
-
-
 @pytest.mark.parametrize("precision", ENGINES)
 @pytest.mark.parametrize("L", [600, 37, 1100])
 def test_bf16_tensor_core_forward_matches_bf16_storage_reference(L, precision):
