@@ -423,13 +423,13 @@ __global__ void __launch_bounds__(CF_THREADS) conv_tc_kernel(const void* __restr
 // K-major no-swizzle layout is eight consecutive rows of one plane (SBO = 128 B between 8-row
 // groups, LBO = plane stride between the two 8-channel halves of a K = 16 step), and the A
 // operand of tap k is the same tile started k rows later: descriptor start + 16 k bytes.  The
-// weights are 36 planes [tap][8-channel group] of [32 co][8 ci].  Per CTA: TPC M tiles of 128
-// positions (128 TPC threads; 18 MMAs per tile, 36 in the backward-data pass, which multiplies the
-// hi and lo parts of its FP32 input) and 32 TPC TMEM columns; warp w reads tile w / 4 at its lane
-// quarter and writes the epilogue (bias + ReLU to BF16, or the FP32 gradient masked by the layer
-// below) straight from registers, one coalesced 32-position store per channel.  Every thread
-// issues all of its staging loads before its first shared store.
-// TPC = M tiles of 128 positions per CTA (1, 2 or 4): 128 TPC threads, four warps per tile
+// weights are 36 planes [tap][8-channel group] of [32 co][8 ci].  A tile is TPC M tiles of 128
+// positions (128 TPC threads; 18 MMAs per M tile, 36 in the backward-data pass, which multiplies
+// the hi and lo parts of its FP32 input) and 32 TPC TMEM columns; warp w reads M tile w / 4 at its
+// lane quarter and writes the epilogue (bias + ReLU to BF16, or the FP32 gradient masked by the
+// layer below) straight from registers, one coalesced 32-position store per channel.  Every
+// thread issues all of its staging loads before its first shared store.
+// TPC = M tiles of 128 positions per tile (1, 2 or 4): 128 TPC threads, four warps per M tile
 template <int TPC> struct C5 {
     static constexpr int CT = 128 * TPC;                   // positions per CTA
     static constexpr int THREADS = 128 * TPC;
@@ -437,7 +437,9 @@ template <int TPC> struct C5 {
     static constexpr int PLANE = XW * 16 + 16;             // bytes per channel plane (+16: planes 4 banks apart)
     static constexpr int PART = 4 * PLANE;                 // one staged part (32 channels)
     static constexpr int COLS = TPC <= 1 ? 32 : 32 * TPC;  // TMEM columns: one N = 32 tile per M tile
-    static constexpr size_t smem(bool fwd) { return (size_t)(fwd ? 1 : 2) * PART + KT * 4 * 512 + 16; }
+    // the persistent convolution: two staging buffers of 1 (forward) or 2 (hi, lo) parts, the
+    // weight planes, two mbarriers and the TMEM address slot
+    static constexpr size_t smem(bool fwd) { return (size_t)2 * (fwd ? 1 : 2) * PART + KT * 4 * 512 + 32; }
     static_assert(PLANE % 16 == 0 && (PLANE / 4) % 32 == 4, "planes 16-byte aligned, four banks apart");
 };
 constexpr int C5_WBYTES = KT * 4 * 512;                    // weight planes
@@ -447,54 +449,54 @@ constexpr int C5_TPC = 2;                                  // the launched shape
 template <int PLANE>
 __device__ __forceinline__ int c5_idx(int j, int c) { return (c >> 3) * (PLANE / 2) + j * 8 + (c & 7); }
 
-// Staging of one row's 32 channels, positions i0 - 4 + j for j < C5_XW (zero outside [0, L)),
-// into planes: the same pieces as stage_act_tile, but every thread issues all of its global loads
-// before its first shared store (the loads come from L2 and would otherwise be waited on one by
-// one).  Called by CF_THREADS threads.
+// Staging of one row's 32 channels, positions i0 - 4 + j for j < XW (zero outside [0, L)), into
+// planes, in two phases so that a pipelined caller keeps the global loads in flight while it does
+// other work: c5_act_load issues every global load of the thread into registers, c5_act_store
+// writes them to the planes.  When L is not a multiple of 8 the 16-byte loads do not apply:
+// c5_act_load does nothing and c5_act_store stages word by word.  Called by THREADS threads.
+template <int TPC> struct C5Act {
+    static constexpr int NITEM = CH * (C5<TPC>::XW / 8 + 1);   // (channel, 8-position block) pieces
+    static constexpr int PER = (NITEM + C5<TPC>::THREADS - 1) / C5<TPC>::THREADS;
+};
+
 template <int TPC>
-__device__ __forceinline__ void c5_stage_act(const unsigned short* __restrict__ rows, int L, int i0, unsigned short* xs)
+__device__ __forceinline__ void c5_act_load(const unsigned short* __restrict__ rows, int L, int i0,
+                                            uint4 (&q)[C5Act<TPC>::PER])
+{
+    constexpr int NITEM = C5Act<TPC>::NITEM, PER = C5Act<TPC>::PER, THREADS = C5<TPC>::THREADS;
+    if ((L & 7) != 0) return;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * THREADS;
+        const int c = e & (CH - 1), v = e / CH;
+        const int pos0 = i0 - 8 + 8 * v;   // a multiple of 8 (i0 is): the piece lies inside [0, L) or outside
+        q[u] = make_uint4(0u, 0u, 0u, 0u);
+        if (e < NITEM && pos0 >= 0 && pos0 + 8 <= L) q[u] = *reinterpret_cast<const uint4*>(rows + (size_t)c * L + pos0);
+    }
+}
+
+template <int TPC>
+__device__ __forceinline__ void c5_act_store(const unsigned short* __restrict__ rows, int L, int i0,
+                                             const uint4 (&q)[C5Act<TPC>::PER], unsigned short* xs)
 {
     using G = C5<TPC>;
-    constexpr int C5_XW = G::XW, CF_THREADS = G::THREADS, P = G::PLANE;
+    constexpr int XW = G::XW, THREADS = G::THREADS, P = G::PLANE;
+    constexpr int NITEM = C5Act<TPC>::NITEM, PER = C5Act<TPC>::PER;
     if ((L & 7) == 0) {
-        constexpr int NITEM = CH * (C5_XW / 8 + 1), PER = (NITEM + CF_THREADS - 1) / CF_THREADS;
-        uint4 q[PER];
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
-            const int e = threadIdx.x + u * CF_THREADS;
-            const int c = e & (CH - 1), v = e / CH;
-            const int pos0 = i0 - 8 + 8 * v;
-            q[u] = make_uint4(0u, 0u, 0u, 0u);
-            if (e < NITEM && pos0 >= 0 && pos0 + 8 <= L)
-                q[u] = *reinterpret_cast<const uint4*>(rows + (size_t)c * L + pos0);
-        }
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int e = threadIdx.x + u * CF_THREADS;
+            const int e = threadIdx.x + u * THREADS;
             if (e >= NITEM) break;
             const int c = e & (CH - 1), v = e / CH;
-            const int pos0 = i0 - 8 + 8 * v;
-            unsigned short t[8];
-            if (pos0 >= 0 && pos0 + 8 <= L) {
-                const uint32_t w[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    t[2 * k] = (unsigned short)(w[k] & 0xffffu);
-                    t[2 * k + 1] = (unsigned short)(w[k] >> 16);
-                }
-            } else {
-                const unsigned short* src = rows + (size_t)c * L;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) t[k] = (pos0 + k >= 0 && pos0 + k < L) ? src[pos0 + k] : 0;
-            }
+            const uint32_t w[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int j = 8 * v - HALF + k;
-                if (j >= 0 && j < C5_XW) xs[c5_idx<P>(j, c)] = t[k];
+                if (j >= 0 && j < XW) xs[c5_idx<P>(j, c)] = (unsigned short)(w[k >> 1] >> (16 * (k & 1)));
             }
         }
     } else {
-        for (int e = threadIdx.x; e < C5_XW * (CH / 2); e += blockDim.x) {
+        for (int e = threadIdx.x; e < XW * (CH / 2); e += THREADS) {
             const int j = e / (CH / 2), cp = e - j * (CH / 2);
             const int pos = i0 - HALF + j;
             const size_t o = (size_t)(2 * cp) * L + pos;
@@ -505,18 +507,28 @@ __device__ __forceinline__ void c5_stage_act(const unsigned short* __restrict__ 
     }
 }
 
-// The same from FP32 rows, split into BF16 hi (part 0) and lo (part 1); loads first, as above.
 template <int TPC>
-__device__ __forceinline__ void c5_stage_split(const float* __restrict__ rows, int L, int i0, unsigned short* xh,
-                                               unsigned short* xl)
+__device__ __forceinline__ void c5_stage_act(const unsigned short* __restrict__ rows, int L, int i0, unsigned short* xs)
 {
-    using G = C5<TPC>;
-    constexpr int C5_XW = G::XW, CF_THREADS = G::THREADS, P = G::PLANE;
-    constexpr int NITEM = CH * (C5_XW / 4), PER = (NITEM + CF_THREADS - 1) / CF_THREADS;
-    float4 q[PER];
+    uint4 q[C5Act<TPC>::PER];
+    c5_act_load<TPC>(rows, L, i0, q);
+    c5_act_store<TPC>(rows, L, i0, q, xs);
+}
+
+// The same from FP32 rows, split into BF16 hi (part xh) and lo (part xl), in the same two phases.
+template <int TPC> struct C5Split {
+    static constexpr int NITEM = CH * (C5<TPC>::XW / 4);        // (channel, 4-position block) pieces
+    static constexpr int PER = (NITEM + C5<TPC>::THREADS - 1) / C5<TPC>::THREADS;
+};
+
+template <int TPC>
+__device__ __forceinline__ void c5_split_load(const float* __restrict__ rows, int L, int i0,
+                                              float4 (&q)[C5Split<TPC>::PER])
+{
+    constexpr int NITEM = C5Split<TPC>::NITEM, PER = C5Split<TPC>::PER, THREADS = C5<TPC>::THREADS;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-        const int e = threadIdx.x + u * CF_THREADS;
+        const int e = threadIdx.x + u * THREADS;
         const int c = e & (CH - 1), v = e / CH;
         const int pos0 = i0 - HALF + 4 * v;
         const float* src = rows + (size_t)c * L;
@@ -532,9 +544,17 @@ __device__ __forceinline__ void c5_stage_split(const float* __restrict__ rows, i
             }
         }
     }
+}
+
+template <int TPC>
+__device__ __forceinline__ void c5_split_store(const float4 (&q)[C5Split<TPC>::PER], unsigned short* xh,
+                                               unsigned short* xl)
+{
+    constexpr int NITEM = C5Split<TPC>::NITEM, PER = C5Split<TPC>::PER, THREADS = C5<TPC>::THREADS;
+    constexpr int P = C5<TPC>::PLANE;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-        const int e = threadIdx.x + u * CF_THREADS;
+        const int e = threadIdx.x + u * THREADS;
         if (e >= NITEM) break;
         const int c = e & (CH - 1), v = e / CH;
         const float t[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
@@ -554,107 +574,170 @@ __device__ __forceinline__ void c5_stage_split(const float* __restrict__ rows, i
 // FWD: in = BF16 activations [B][32][L], out = BF16 relu(conv + bias).
 // !FWD: in = FP32 gradient [B][32][L], out = FP32 conv masked by mask > 0, no bias.
 // wt: GEMM rows [out channel][tap][in channel] (BF16), as for conv_tc_kernel.
-template <bool FWD, int TPC>
-__global__ void __launch_bounds__(C5<TPC>::THREADS) conv_tc05_kernel(const void* __restrict__ in,
-                                                               const __nv_bfloat16* __restrict__ wt,
-                                                               const float* __restrict__ bias,
-                                                               const __nv_bfloat16* __restrict__ mask, int L,
-                                                               void* __restrict__ out)
+// Persistent: CTA c takes tiles c, c + gridDim.x, ... of the n_rows x ceil(L / CT) tiles (row-major)
+// with a two-deep pipeline over two staging buffers, two TMEM accumulators and two mbarriers.  In
+// the iteration of tile t: the global loads of tile t + gridDim.x are issued into registers, the
+// epilogue of tile t runs (its MMAs were issued one iteration earlier), the registers are written
+// to the other staging buffer (whose MMAs completed before the previous epilogue), and after one
+// barrier thread 0 issues that tile's MMAs into the other accumulator.  The weights are staged
+// once per CTA.  A wait that runs out of polls ends the CTA's loop (the vote at the barrier makes
+// that uniform) and the tiles left are not written.
+constexpr int C5_CTAS_PER_SM = 2;
+static_assert(C5_CTAS_PER_SM * 2 * C5<C5_TPC>::COLS <= 512, "TMEM columns of the resident CTAs");
+template <bool FWD>
+__global__ void __launch_bounds__(C5<C5_TPC>::THREADS, C5_CTAS_PER_SM) conv_tc05_kernel(const void* __restrict__ in,
+                                                                         const __nv_bfloat16* __restrict__ wt,
+                                                                         const float* __restrict__ bias,
+                                                                         const __nv_bfloat16* __restrict__ mask, int L,
+                                                                         int n_rows, void* __restrict__ out)
 {
-    using G = C5<TPC>;
+    using G = C5<C5_TPC>;
     constexpr int NX = FWD ? 1 : 2;
     constexpr int C5_CT = G::CT, CF_THREADS = G::THREADS, C5_PART = G::PART, C5_PLANE = G::PLANE, C5_COLS = G::COLS;
     static_assert(C5_PLANE % 16 == 0 && C5_PART % 16 == 0, "descriptor steps are whole 16-byte units");
     extern __shared__ __align__(128) unsigned char c5_smem[];
-    unsigned char* xs = c5_smem;                                  // NX parts of 4 planes
-    unsigned char* ws = c5_smem + NX * C5_PART;                   // 36 weight planes
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(ws + C5_WBYTES);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(ws + C5_WBYTES + 8);
-    const int b = blockIdx.y, i0 = blockIdx.x * C5_CT;
+    unsigned char* xs = c5_smem;                                  // [2 buffers][NX parts of 4 planes]
+    unsigned char* ws = c5_smem + 2 * NX * C5_PART;               // 36 weight planes
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(ws + C5_WBYTES); // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    if (tid == 0) isr::mbar_init(isr::smem_u32(mbar), 1);
-    if (warp == 0) isr::tmem_alloc(isr::smem_u32(tslot), C5_COLS);
-    // weights: 16-byte piece (co, tap, 8-channel group g) of row co to plane (tap, g), row co
-    const uint4* w4 = reinterpret_cast<const uint4*>(wt);
-    constexpr int WPER = (CH * KT * 4 + CF_THREADS - 1) / CF_THREADS;
-    uint4 wq[WPER];
-#pragma unroll
-    for (int u = 0; u < WPER; ++u) {
-        const int e = tid + u * CF_THREADS;
-        if (e < CH * KT * 4) wq[u] = w4[e];
-    }
-#pragma unroll
-    for (int u = 0; u < WPER; ++u) {
-        const int e = tid + u * CF_THREADS;
-        if (e >= CH * KT * 4) break;
-        const int co = e / (KT * 4), r = e - co * (KT * 4);      // r = tap * 4 + g
-        *reinterpret_cast<uint4*>(ws + (r * CH + co) * 16) = wq[u];
-    }
-    if constexpr (FWD)
-        c5_stage_act<TPC>(static_cast<const unsigned short*>(in) + (size_t)b * CH * L, L, i0,
-                     reinterpret_cast<unsigned short*>(xs));
-    else
-        c5_stage_split<TPC>(static_cast<const float*>(in) + (size_t)b * CH * L, L, i0, reinterpret_cast<unsigned short*>(xs),
-                       reinterpret_cast<unsigned short*>(xs + C5_PART));
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the tiles, for the tensor cores
-    isr::fence_barrier_init();
-    isr::tmem_fence_before_sync();
-    __syncthreads();
-    isr::tmem_fence_after_sync();
-    const uint32_t tbase = *tslot;
+    const int tiles_per_row = (L + C5_CT - 1) / C5_CT, n_tiles = n_rows * tiles_per_row;
+    if ((int)blockIdx.x >= n_tiles) return;   // uniform per CTA, before any barrier or allocation
 
     if (tid == 0) {
+        isr::mbar_init(isr::smem_u32(&mbar[0]), 1);
+        isr::mbar_init(isr::smem_u32(&mbar[1]), 1);
+    }
+    if (warp == 0) isr::tmem_alloc(isr::smem_u32(tslot), 2 * C5_COLS);
+    // weights: 16-byte piece (co, tap, 8-channel group g) of row co to plane (tap, g), row co
+    {
+        const uint4* w4 = reinterpret_cast<const uint4*>(wt);
+        constexpr int WPER = (CH * KT * 4 + CF_THREADS - 1) / CF_THREADS;
+        uint4 wq[WPER];
+#pragma unroll
+        for (int u = 0; u < WPER; ++u) {
+            const int e = tid + u * CF_THREADS;
+            if (e < CH * KT * 4) wq[u] = w4[e];
+        }
+#pragma unroll
+        for (int u = 0; u < WPER; ++u) {
+            const int e = tid + u * CF_THREADS;
+            if (e >= CH * KT * 4) break;
+            const int co = e / (KT * 4), r = e - co * (KT * 4);  // r = tap * 4 + g
+            *reinterpret_cast<uint4*>(ws + (r * CH + co) * 16) = wq[u];
+        }
+    }
+
+    // staging of tile t: global loads into registers, then shared stores into buffer `buf`
+    uint4 qa[FWD ? C5Act<C5_TPC>::PER : 1];
+    float4 qs[FWD ? 1 : C5Split<C5_TPC>::PER];
+    auto load = [&](int t) {
+        const int b = t / tiles_per_row, i0 = (t - b * tiles_per_row) * C5_CT;
+        if constexpr (FWD)
+            c5_act_load<C5_TPC>(static_cast<const unsigned short*>(in) + (size_t)b * CH * L, L, i0, qa);
+        else
+            c5_split_load<C5_TPC>(static_cast<const float*>(in) + (size_t)b * CH * L, L, i0, qs);
+    };
+    auto store = [&](int t, int buf) {
+        const int b = t / tiles_per_row, i0 = (t - b * tiles_per_row) * C5_CT;
+        unsigned char* x = xs + buf * NX * C5_PART;
+        if constexpr (FWD)
+            c5_act_store<C5_TPC>(static_cast<const unsigned short*>(in) + (size_t)b * CH * L, L, i0, qa,
+                                 reinterpret_cast<unsigned short*>(x));
+        else
+            c5_split_store<C5_TPC>(qs, reinterpret_cast<unsigned short*>(x), reinterpret_cast<unsigned short*>(x + C5_PART));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the tile, for the tensor cores
+    };
+    // thread 0: the MMAs of the tile in buffer `buf` into accumulator `buf`, committed to mbar[buf]
+    auto issue = [&](uint32_t tbase, int buf) {
         constexpr uint32_t idesc = isr::tc05_idesc<true>();      // BF16, FP32 accumulate, M 128, N 32
         // descriptors built once and stepped in 16-byte units of the start field (addresses stay
         // below 0x40000 B, so the 14-bit field never carries): tap k starts the A tile k rows
         // (16 B each) later and B at weight plane 4 k; K-step ks moves A by two channel planes
         // and B by two weight planes (512 B each)
         const uint64_t bd0 = isr::tc05_desc(isr::smem_u32(ws), 512, 128);
+        const uint32_t xb = isr::smem_u32(xs) + buf * NX * C5_PART;
 #pragma unroll 1
         for (int m = 0; m < C5_CT / 128; ++m) {
+            const uint32_t d = tbase + (uint32_t)(buf * C5_COLS) + 32u * m;
             uint32_t acc = 0;
 #pragma unroll 1
             for (int part = 0; part < NX; ++part) {
                 // rows 128 m + tap of the tile, channels 16 ks .. (planes 2 ks, 2 ks + 1)
-                const uint64_t ad0 = isr::tc05_desc(isr::smem_u32(xs) + part * C5_PART + 128 * m * 16, C5_PLANE, 128);
+                const uint64_t ad0 = isr::tc05_desc(xb + part * C5_PART + 128 * m * 16, C5_PLANE, 128);
 #pragma unroll
                 for (int tap = 0; tap < KT; ++tap)
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
-                        isr::tc05_mma(tbase + 32u * m, ad0 + (uint32_t)(tap + ks * (2 * C5_PLANE / 16)),
+                        isr::tc05_mma(d, ad0 + (uint32_t)(tap + ks * (2 * C5_PLANE / 16)),
                                       bd0 + (uint32_t)((tap * 4 + 2 * ks) * (512 / 16)), idesc, acc);
                         acc = 1;
                     }
             }
         }
-        isr::tc05_commit(isr::smem_u32(mbar));
-    }
-    const bool done = isr::mbar_wait(isr::smem_u32(mbar), 0, 1u << 26);
+        isr::tc05_commit(isr::smem_u32(&mbar[buf]));
+    };
+
+    int t = blockIdx.x;
+    load(t);
+    store(t, 0);
+    isr::fence_barrier_init();
+    isr::tmem_fence_before_sync();
+    __syncthreads();
     isr::tmem_fence_after_sync();
+    const uint32_t tbase = *tslot;
+    if (tid == 0) issue(tbase, 0);
 
     // epilogue: warp w, tile m = w / 4, lane quarter w % 4 -> position i
     const int m = warp >> 2;
-    const int i = i0 + 128 * m + 32 * (warp & 3) + lane;
-    uint32_t r[32];
-    isr::tmem_ld32(isr::tmem_warp_lane_base(tbase) + 32u * m, r);
-    isr::tmem_wait_ld32(r);
-    if (done && i < L) {
-        const size_t row = (size_t)b * CH * L + i;
+    for (int k = 0;; ++k) {
+        const int buf = k & 1, tn = t + (int)gridDim.x;
+        const bool more = tn < n_tiles;
+        if (more) load(tn);
+        const bool done = isr::mbar_wait(isr::smem_u32(&mbar[buf]), (uint32_t)(k >> 1) & 1u, 1u << 26);
+        isr::tmem_fence_after_sync();
+        {
+            const int b = t / tiles_per_row, i0 = (t - b * tiles_per_row) * C5_CT;
+            const int i = i0 + 128 * m + 32 * (warp & 3) + lane;
+            uint32_t r[32];
+            isr::tmem_ld32(isr::tmem_warp_lane_base(tbase) + (uint32_t)(buf * C5_COLS) + 32u * m, r);
+            isr::tmem_wait_ld32(r);
+            if (done && i < L) {
+                const size_t row = (size_t)b * CH * L + i;
 #pragma unroll
-        for (int co = 0; co < CH; ++co) {
-            const float v = __uint_as_float(r[co]);
-            if constexpr (FWD) {
-                static_cast<__nv_bfloat16*>(out)[row + (size_t)co * L] = __float2bfloat16_rn(fmaxf(v + __ldg(bias + co), 0.f));
-            } else {
-                static_cast<float*>(out)[row + (size_t)co * L] = __bfloat162float(mask[row + (size_t)co * L]) > 0.f ? v : 0.f;
+                for (int co = 0; co < CH; ++co) {
+                    const float v = __uint_as_float(r[co]);
+                    if constexpr (FWD) {
+                        static_cast<__nv_bfloat16*>(out)[row + (size_t)co * L] =
+                            __float2bfloat16_rn(fmaxf(v + __ldg(bias + co), 0.f));
+                    } else {
+                        static_cast<float*>(out)[row + (size_t)co * L] =
+                            __bfloat162float(mask[row + (size_t)co * L]) > 0.f ? v : 0.f;
+                    }
+                }
             }
         }
+        // the other staging buffer and accumulator were last used by tile t - gridDim.x, whose
+        // MMAs completed (waited on in the previous iteration) and whose epilogue is done
+        if (more) store(tn, buf ^ 1);
+        isr::tmem_fence_before_sync();
+        const bool ok = __syncthreads_and(done) != 0;
+        isr::tmem_fence_after_sync();
+        if (!more || !ok) break;
+        if (tid == 0) issue(tbase, buf ^ 1);
+        t = tn;
     }
     isr::tmem_fence_before_sync();
     __syncthreads();
     isr::tmem_fence_after_sync();
-    if (warp == 0) isr::tmem_dealloc(tbase, C5_COLS);
+    if (warp == 0) isr::tmem_dealloc(tbase, 2 * C5_COLS);
+}
+
+// Persistent CTAs of conv_tc05_kernel: one per tile, up to `slots` (the resident count on all SMs).
+inline int conv_tc05_grid(int L, int n_rows, int slots)
+{
+    const int tiles = n_rows * ((L + C5<C5_TPC>::CT - 1) / C5<C5_TPC>::CT);
+    return std::max(1, std::min(tiles, slots));
 }
 
 __device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], uint32_t addr)
@@ -1385,6 +1468,7 @@ struct isr_est {
     int wgrad_slots = 0;                      // resident tensor-core weight-gradient CTAs (all SMs)
     bool conv05 = false;                      // BF16 convolutions on tcgen05 (else mma.sync)
     int sms = 0;                              // multiprocessors of the device
+    int c5_slots[2] = {1, 1};                 // persistent tcgen05 convolution CTAs, backward / forward
     int* pidx = nullptr;
     float *da0 = nullptr, *da1 = nullptr; // gradient ping-pong [B][32][L]
 };
@@ -1430,10 +1514,14 @@ isr_status set_smem_attrs()
                                      (int)wgrad_tc_smem_bytes()));
         EST_TRY(cudaFuncSetAttribute(wgrad_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)W5_SMEM_LAUNCH));
-        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<true, C5_TPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)C5<C5_TPC>::smem(true)));
-        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<false, C5_TPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)C5<C5_TPC>::smem(false)));
+        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
+        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
     }
     return ISR_OK;
 }
@@ -1460,9 +1548,9 @@ isr_status forward_t(isr_est* e, const float* x, int n, float* pos = nullptr, fl
         if constexpr (kTensorConv<T>) {
             const T* w = static_cast<const T*>(e->tf) + (size_t)(l - 2) * CH * CH * KT;
             if (e->conv05)
-                conv_tc05_kernel<true, C5_TPC><<<dim3((L + C5<C5_TPC>::CT - 1) / C5<C5_TPC>::CT, n), C5<C5_TPC>::THREADS,
-                                                 C5<C5_TPC>::smem(true), s>>>(
-                    act[l - 1], w, e->theta + b_off(l), nullptr, L, act[l]);
+                conv_tc05_kernel<true><<<conv_tc05_grid(L, n, e->c5_slots[1]), C5<C5_TPC>::THREADS,
+                                         C5<C5_TPC>::smem(true), s>>>(act[l - 1], w, e->theta + b_off(l), nullptr, L, n,
+                                                                      act[l]);
             else
                 conv_tc_kernel<true><<<dim3((L + CF_CT - 1) / CF_CT, n), CF_THREADS, tc_smem_bytes(true), s>>>(
                     act[l - 1], w, e->theta + b_off(l), nullptr, L, act[l]);
@@ -1519,9 +1607,8 @@ isr_status backward_t(isr_est* e, int n, const float* fpos, const float* pres)
             if constexpr (kTensorConv<T>) {
                 const T* w = static_cast<const T*>(e->tb) + (size_t)(l - 2) * CH * CH * KT;
                 if (e->conv05)
-                    conv_tc05_kernel<false, C5_TPC><<<dim3((L + C5<C5_TPC>::CT - 1) / C5<C5_TPC>::CT, n),
-                                                      C5<C5_TPC>::THREADS, C5<C5_TPC>::smem(false), s>>>(
-                        da, w, nullptr, act[l - 1], L, dn);
+                    conv_tc05_kernel<false><<<conv_tc05_grid(L, n, e->c5_slots[0]), C5<C5_TPC>::THREADS,
+                                              C5<C5_TPC>::smem(false), s>>>(da, w, nullptr, act[l - 1], L, n, dn);
                 else
                     conv_tc_kernel<false><<<dim3((L + CF_CT - 1) / CF_CT, n), CF_THREADS, tc_smem_bytes(false), s>>>(
                         da, w, nullptr, act[l - 1], L, dn);
@@ -1631,6 +1718,9 @@ isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t 
                 r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wgrad_tc_kernel, 256, wgrad_tc_smem_bytes());
             e->wgrad_slots = std::max(1, occ) * std::max(1, sms);
             e->sms = std::max(1, sms);
+            // two CTAs per SM, the shape the kernel is built for (__launch_bounds__ minimum): 128
+            // registers x 256 threads, at most 86 KB of shared memory and 128 TMEM columns each
+            e->c5_slots[0] = e->c5_slots[1] = C5_CTAS_PER_SM * e->sms;
         }
     }
     if (r != cudaSuccess) {
