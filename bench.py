@@ -364,7 +364,8 @@ def run_ours(args):
         e2e_ms = max_over_ranks([e2e_ms], dev, world, use_dist)[0]
         e2e = {"value": job_throughput(world, R_total if strong else R, P, e2e_ms, strong), "unit": UNIT,
                "h2d_bytes_per_step": int(echo_h.numel() * 2 + code_h.numel()),
-               "d2h_bytes_per_step": int(out_h.numel() * 4), "ms_per_step": e2e_ms}
+               "d2h_bytes_per_step": int(out_h.numel() * 4), "ms_per_step": e2e_ms,
+               "host_block_growth": plan.info()["host_block_growth"]}
         del echo_h
 
     ms, kernel_ms = max_over_ranks([ms, kernel_ms], dev, world, use_dist)

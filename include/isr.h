@@ -85,6 +85,8 @@ typedef struct {
     int64_t kernel_launches;   /* fused-kernel launches since creation */
     double kernel_ms;          /* summed fused-kernel time of timed launches (profiling) */
     int64_t kernel_timed;      /* launches counted in kernel_ms */
+    int64_t host_block_growth; /* growth of the host-input blocks the last call with host rows
+                                  beyond one staging buffer measured (1..4; 0: no such call) */
 } isr_plan_info;
 
 typedef struct isr_plan isr_plan;

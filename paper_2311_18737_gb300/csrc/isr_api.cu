@@ -155,6 +155,8 @@ struct isr_plan {
     int64_t hs_rows = 0;
     cudaEvent_t hs_copied[2] = {nullptr, nullptr};
     cudaEvent_t hs_free[2] = {nullptr, nullptr};
+    cudaEvent_t hs_t[4] = {nullptr, nullptr, nullptr, nullptr};   // block 0: copy start / end, kernels start / end
+    int64_t hs_growth = 0;    // block growth the last multi-block host-input call measured (0: none yet)
 };
 
 namespace {
@@ -281,6 +283,8 @@ isr_status ensure_host_staging(isr_plan* p, int64_t rows)
         if (!p->hs_copied[b]) CUDA_TRY(cudaEventCreateWithFlags(&p->hs_copied[b], cudaEventDisableTiming));
         if (!p->hs_free[b]) CUDA_TRY(cudaEventCreateWithFlags(&p->hs_free[b], cudaEventDisableTiming));
     }
+    for (auto& e : p->hs_t)
+        if (!e) CUDA_TRY(cudaEventCreate(&e));
     if (!p->copy_stream) CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
     p->hs_rows = rows;
     return ISR_OK;
@@ -298,16 +302,23 @@ isr_status integrate_host(isr_plan* p, const int16_t* echo, const void* tx, int6
     const int cb = chip_bytes(p->d.tx_type);
     const char* txc = static_cast<const char*>(tx);
     bool tx_dev = is_device_ptr(tx);
-    // a call larger than one staging buffer starts with a small block, so the kernels get going
-    // after a short copy, and the blocks then grow 4x up to a buffer: each copy stays shorter
-    // than the kernels of the block before it even on a slow host link, with few launches
-    // (each ends with a partly filled wave); a call that fits one buffer is one block
-    int64_t cur = n > rows ? std::max<int64_t>(1, std::min<int64_t>(rows, kHostFirstBytes / row_bytes)) : rows;
+    // A call larger than one staging buffer starts with a small block, so the kernels get going
+    // after a short copy, and the blocks then grow up to a buffer, with few launches (each ends
+    // with a partly filled wave).  The copy of block i + 1 stays hidden behind block i's kernels
+    // while growth <= (kernel time) / (copy time) of equal blocks; the host link differs from box
+    // to box, so block 0's copy and kernels are timed, block 1 doubles meanwhile, and once block 1
+    // is queued the host waits for block 0's kernels and takes growth = that ratio, within 1..4.
+    // A call that fits one buffer is one block.
+    const bool several = n > rows;
+    int64_t cur = several ? std::max<int64_t>(1, std::min<int64_t>(rows, kHostFirstBytes / row_bytes)) : rows;
+    int64_t growth = 2;
     int blk = 0;
-    for (int64_t done = 0, nb = 0; done < n; done += nb, ++blk, cur = std::min<int64_t>(rows, 4 * cur)) {
+    for (int64_t done = 0, nb = 0; done < n; done += nb, ++blk, cur = std::min<int64_t>(rows, growth * cur)) {
         const int b = blk & 1;
         nb = std::min(cur, n - done);
+        const bool time0 = several && blk == 0;
         CUDA_TRY(cudaStreamWaitEvent(p->copy_stream, p->hs_free[b], 0));
+        if (time0) CUDA_TRY(cudaEventRecord(p->hs_t[0], p->copy_stream));
         CUDA_TRY(cudaMemcpyAsync(p->hs_echo[b], echo + done * p->d.echo_stride * 2, (size_t)(nb * row_bytes),
                                  cudaMemcpyHostToDevice, p->copy_stream));
         const char* txblk;
@@ -321,10 +332,22 @@ isr_status integrate_host(isr_plan* p, const int16_t* echo, const void* tx, int6
             txblk = p->hs_tx[b];
         }
         CUDA_TRY(cudaEventRecord(p->hs_copied[b], p->copy_stream));
+        if (time0) CUDA_TRY(cudaEventRecord(p->hs_t[1], p->copy_stream));
         CUDA_TRY(cudaStreamWaitEvent(p->stream, p->hs_copied[b], 0));
+        if (time0) CUDA_TRY(cudaEventRecord(p->hs_t[2], p->stream));
         st = launch_block(p, p->hs_echo[b], txblk, nb, start, step);
         if (st != ISR_OK) return st;
+        if (time0) CUDA_TRY(cudaEventRecord(p->hs_t[3], p->stream));
         CUDA_TRY(cudaEventRecord(p->hs_free[b], p->stream));
+        if (several && blk == 1) {
+            // block 1 is queued, so the GPU stays busy while the host waits for block 0's kernels
+            float tc = 0.f, tk = 0.f;
+            CUDA_TRY(cudaEventSynchronize(p->hs_t[3]));
+            CUDA_TRY(cudaEventElapsedTime(&tc, p->hs_t[0], p->hs_t[1]));
+            CUDA_TRY(cudaEventElapsedTime(&tk, p->hs_t[2], p->hs_t[3]));
+            growth = tc > 0.f ? std::max<int64_t>(1, std::min<int64_t>(4, (int64_t)(tk / tc))) : 4;
+            p->hs_growth = growth;
+        }
     }
     CUDA_TRY(cudaStreamSynchronize(p->copy_stream));
     return ISR_OK;
@@ -502,6 +525,7 @@ isr_status isr_plan_query(const isr_plan* p, isr_plan_info* info)
     info->kernel_launches = p->launches;
     info->kernel_ms = p->kernel_ms;
     info->kernel_timed = p->kernel_timed;
+    info->host_block_growth = p->hs_growth;
     return ISR_OK;
 }
 
@@ -727,6 +751,8 @@ void isr_destroy(isr_plan* p)
         if (p->hs_copied[b]) cudaEventDestroy(p->hs_copied[b]);
         if (p->hs_free[b]) cudaEventDestroy(p->hs_free[b]);
     }
+    for (auto e : p->hs_t)
+        if (e) cudaEventDestroy(e);
     cudaFree(p->acc);
     cudaFree(p->partial);
     cudaFree(p->status);

@@ -454,16 +454,17 @@ __device__ __forceinline__ int c5_idx(int j, int c) { return (c >> 3) * (PLANE /
 // other work: c5_act_load issues every global load of the thread into registers, c5_act_store
 // writes them to the planes.  When L is not a multiple of 8 the 16-byte loads do not apply:
 // c5_act_load does nothing and c5_act_store stages word by word.  Called by THREADS threads.
-template <int TPC> struct C5Act {
+// NT = the calling threads (C5<TPC>::THREADS unless a caller stages with more).
+template <int TPC, int NT = C5<TPC>::THREADS> struct C5Act {
     static constexpr int NITEM = CH * (C5<TPC>::XW / 8 + 1);   // (channel, 8-position block) pieces
-    static constexpr int PER = (NITEM + C5<TPC>::THREADS - 1) / C5<TPC>::THREADS;
+    static constexpr int PER = (NITEM + NT - 1) / NT;
 };
 
-template <int TPC>
+template <int TPC, int NT = C5<TPC>::THREADS>
 __device__ __forceinline__ void c5_act_load(const unsigned short* __restrict__ rows, int L, int i0,
-                                            uint4 (&q)[C5Act<TPC>::PER])
+                                            uint4 (&q)[C5Act<TPC, NT>::PER])
 {
-    constexpr int NITEM = C5Act<TPC>::NITEM, PER = C5Act<TPC>::PER, THREADS = C5<TPC>::THREADS;
+    constexpr int NITEM = C5Act<TPC, NT>::NITEM, PER = C5Act<TPC, NT>::PER, THREADS = NT;
     if ((L & 7) != 0) return;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
@@ -475,13 +476,13 @@ __device__ __forceinline__ void c5_act_load(const unsigned short* __restrict__ r
     }
 }
 
-template <int TPC>
+template <int TPC, int NT = C5<TPC>::THREADS>
 __device__ __forceinline__ void c5_act_store(const unsigned short* __restrict__ rows, int L, int i0,
-                                             const uint4 (&q)[C5Act<TPC>::PER], unsigned short* xs)
+                                             const uint4 (&q)[C5Act<TPC, NT>::PER], unsigned short* xs)
 {
     using G = C5<TPC>;
-    constexpr int XW = G::XW, THREADS = G::THREADS, P = G::PLANE;
-    constexpr int NITEM = C5Act<TPC>::NITEM, PER = C5Act<TPC>::PER;
+    constexpr int XW = G::XW, THREADS = NT, P = G::PLANE;
+    constexpr int NITEM = C5Act<TPC, NT>::NITEM, PER = C5Act<TPC, NT>::PER;
     if ((L & 7) == 0) {
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
@@ -858,60 +859,85 @@ __global__ void __launch_bounds__(256, 4) wgrad_tc_kernel(const __nv_bfloat16* _
 }
 
 // Weight gradient of layers 2-4 on tcgen05 (ISR_EST_BF16):
-//   dW[co][ci][k] = sum_p da[co][p] h[ci][p + k - 4]   over the CTA's span of one row,
-// as D[row][32 k + ci] = sum_p A[row][p] B_k[ci][p] with K = positions (16 per MMA), rows 0-31 the
-// BF16 hi parts of da and rows 32-63 its lo parts (their sum keeps ~16 bits of the FP32
-// gradient), N = 32 per tap (TMEM columns 32 k, 288 in all).  In the no-swizzle layouts of both
-// majors the descriptor's leading-byte offset steps along K and its stride-byte offset along
-// M or N.  A is K-major: 8 x 8 blocks
-// [8 channels][8 positions] staged straight from the channel-major rows; rows 64-127 of the
-// M = 128 instruction read whatever lies beyond the real rows (the next staging buffer or the
-// activation tiles) and land in accumulator rows that are never read.  B_k is the activation tile
-// in its position-major planes (MN-major: 8 channels per 16-byte row, positions as rows), started
-// k rows later for tap k.  Chunks of 256 positions are double-buffered: while the tensor core
-// runs one chunk's 144 MMAs, the CTA stages the next.  One CTA per SM (512 TMEM columns).
+//   dW[co][ci][k] = sum_p da[co][p] h[ci][p + k - 4]   over the CTA's chunks,
+// as D_g[(k, i)][n] = sum_p A_g[(k, i)][p] B[n][p] with K = positions (16 per MMA): A_g = the
+// activation planes of channel group g (8 channels per 16-byte row, positions as rows) as an
+// MN-major operand whose 8-row M-groups are 16 bytes apart, so M-group k reads channels 8 g + i at
+// position p + k, i.e. tap k (groups 9-15 are padding); B = the gradient's BF16 hi parts (rows
+// 0-31) and lo parts (rows 32-63; their sum keeps ~16 bits of the FP32 gradient), K-major 8 x 8
+// blocks staged from the channel-major rows; N = 64, M = 128, TMEM columns 64 g, 256 in all.  In
+// the no-swizzle layouts of both majors the descriptor's leading-byte offset steps along K and its
+// stride-byte offset along M or N.  Four 128 x 64 x 16 MMAs per K-step (64 per chunk) read 6 KB of
+// shared memory each: 384 KB per chunk, where 32-column MMAs per tap needed 144 MMAs and 720 KB,
+// which the tensor pipe could not stream while the CTA staged the next chunk.  Chunks of 256
+// positions are double-buffered; 16 warps stage (and run the epilogue), one more issues the MMAs;
+// the n_rows x ceil(L / 256) chunks, row after row, are split into gridDim.x contiguous ranges of
+// equal length (+-1), so a CTA's range may cross from one row into the next: the sum over
+// positions and rows does not care.  One CTA per SM.
+// one arrival (release semantics at CTA scope) on the barrier's current phase
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 constexpr int W5_CHUNK = 256;                    // positions per chunk (16 K-steps)
-constexpr int W5_THREADS = 256;
+constexpr int W5_THREADS = 512;                  // staging (and epilogue) threads
+constexpr int W5_BLOCK = W5_THREADS + 32;        // + one warp that issues the MMAs
 constexpr int W5_ASBO = W5_CHUNK / 8 * 128;      // bytes per 8-row group of A (all its 8-position blocks)
 constexpr int W5_ABUF = 8 * W5_ASBO;             // one A buffer: 8 real row groups (hi 0-3, lo 4-7)
 using W5X = C5<2>;                               // activation tile: 256 + 8 rows, 4 planes
-static_assert(W5X::CT == W5_CHUNK && W5X::THREADS == W5_THREADS, "activation tile matches the chunk");
+static_assert(W5X::CT == W5_CHUNK, "activation tile matches the chunk");
 constexpr size_t w5_smem_bytes() { return (size_t)2 * W5_ABUF + 2 * W5X::PART + 64; }
-// dynamic shared memory requested at launch: more than half an SM's, so that one CTA (and its 512
-// TMEM columns) has the SM to itself and no second CTA waits in tcgen05.alloc
+// dynamic shared memory requested at launch: more than half an SM's, so that one CTA has the SM to
+// itself (its 544 threads need the register file)
 constexpr size_t W5_SMEM_LAUNCH = 120 * 1024;
+constexpr int W5_TMEM_COLS = 4 * 2 * CH;         // D_g of the four channel groups
 static_assert(w5_smem_bytes() <= W5_SMEM_LAUNCH, "launch request covers the layout");
-// rows 64-127 of either A buffer stay inside the allocation
-static_assert((size_t)W5_ABUF + 16 * W5_ASBO <= 2 * W5_ABUF + 2 * W5X::PART, "A's unused rows stay in shared memory");
+// the padding M-groups (taps 9-15) of the last plane of the second buffer read up to 4336 bytes
+// from that plane's start: still inside the launch allocation
+static_assert((size_t)2 * W5_ABUF + W5X::PART + 3 * W5X::PLANE + (W5_CHUNK - 16) * 16 + 15 * 16 + 256 <= W5_SMEM_LAUNCH,
+              "A's padding rows stay in shared memory");
+// ... and the 9 real taps stay inside their plane (rows < XW)
+static_assert((W5_CHUNK - 16) + 15 + (KT - 1) < W5X::XW, "real taps read staged rows only");
 
-__global__ void __launch_bounds__(W5_THREADS, 1) wgrad_tc05_kernel(const __nv_bfloat16* __restrict__ h,
-                                                                   const float* __restrict__ da, int L, int span,
+__global__ void __launch_bounds__(W5_BLOCK, 1) wgrad_tc05_kernel(const __nv_bfloat16* __restrict__ h,
+                                                                   const float* __restrict__ da, int L, int n_rows,
                                                                    float* __restrict__ dW, float* __restrict__ db)
 {
     extern __shared__ __align__(128) unsigned char w5_smem[];
     unsigned char* abuf = w5_smem;                                  // [2][8 row groups][W5_ASBO]
     unsigned char* xbuf = w5_smem + 2 * W5_ABUF;                    // [2][W5X::PART]
+    // mbar[b]: the MMAs of the chunk in buffer b completed (one commit); full[b]: buffer b staged
+    // (one arrival per staging warp)
     uint64_t* mbar = reinterpret_cast<uint64_t*>(w5_smem + 2 * W5_ABUF + 2 * W5X::PART);   // [2]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    uint64_t* full = mbar + 2;                                                              // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 4);
     __shared__ float db_s[CH];
-    const int b = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int p_begin = blockIdx.x * span, span_end = min(L, p_begin + span);
-    const int nch = (span_end - p_begin + W5_CHUNK - 1) / W5_CHUNK;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cpr = (L + W5_CHUNK - 1) / W5_CHUNK;                 // chunks per row
+    const int64_t total = (int64_t)n_rows * cpr;
+    const int q_begin = (int)((int64_t)blockIdx.x * total / gridDim.x);
+    const int nch = (int)((int64_t)(blockIdx.x + 1) * total / gridDim.x) - q_begin;
     if (tid < CH) db_s[tid] = 0.f;
     if (tid == 0) {
         isr::mbar_init(isr::smem_u32(&mbar[0]), 1);
         isr::mbar_init(isr::smem_u32(&mbar[1]), 1);
+        isr::mbar_init(isr::smem_u32(&full[0]), W5_THREADS / 32);
+        isr::mbar_init(isr::smem_u32(&full[1]), W5_THREADS / 32);
     }
-    if (warp == 0) isr::tmem_alloc(isr::smem_u32(tslot), 512);
+    if (warp == 0) isr::tmem_alloc(isr::smem_u32(tslot), W5_TMEM_COLS);
 
-    // stage chunk c into buffer c & 1: da as hi / lo 8 x 8 blocks, the activations as planes
-    auto stage = [&](int c) {
-        const int p0 = p_begin + c * W5_CHUNK;
-        unsigned char* a = abuf + (c & 1) * W5_ABUF;
-        // items (8-position block kb, channel co) with the channel fastest: the eight lanes of a
-        // 16-byte store phase write one 128-byte core matrix (no bank conflicts)
-        constexpr int NITEM = CH * (W5_CHUNK / 8), PER = NITEM / W5_THREADS;
-        float4 q0[PER], q1[PER];
+    // stage chunk c into buffer c & 1: da as hi / lo 8 x 8 blocks, the activations as planes; in
+    // two phases, all global loads of the chunk (gradient and activations) into registers first,
+    // then the shared stores, so that one round trip to memory per chunk overlaps the MMAs
+    // items (8-position block kb, channel co) with the channel fastest: the eight lanes of a
+    // 16-byte store phase write one 128-byte core matrix (no bank conflicts)
+    constexpr int NITEM = CH * (W5_CHUNK / 8), PER = NITEM / W5_THREADS;
+    float4 q0[PER], q1[PER];
+    uint4 qa[C5Act<2, W5_THREADS>::PER];
+    auto load = [&](int c) {
+        const int q = q_begin + c, b = q / cpr, p0 = (q - b * cpr) * W5_CHUNK;
+        const int span_end = min(L, p0 + W5_CHUNK);
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int e = tid + u * W5_THREADS;
@@ -929,6 +955,11 @@ __global__ void __launch_bounds__(W5_THREADS, 1) wgrad_tc05_kernel(const __nv_bf
                 q1[u] = make_float4(t[4], t[5], t[6], t[7]);
             }
         }
+        c5_act_load<2, W5_THREADS>(reinterpret_cast<const unsigned short*>(h) + (size_t)b * CH * L, L, p0, qa);
+    };
+    auto store = [&](int c) {
+        const int q = q_begin + c, b = q / cpr, p0 = (q - b * cpr) * W5_CHUNK;
+        unsigned char* a = abuf + (c & 1) * W5_ABUF;
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int e = tid + u * W5_THREADS;
@@ -943,68 +974,89 @@ __global__ void __launch_bounds__(W5_THREADS, 1) wgrad_tc05_kernel(const __nv_bf
             // bias gradient (lane = channel: 32 distinct shared addresses per warp)
             atomicAdd(&db_s[co], ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7])));
         }
-        c5_stage_act<2>(reinterpret_cast<const unsigned short*>(h) + (size_t)b * CH * L, L, p0,
-                        reinterpret_cast<unsigned short*>(xbuf + (c & 1) * W5X::PART));
+        c5_act_store<2, W5_THREADS>(reinterpret_cast<const unsigned short*>(h) + (size_t)b * CH * L, L, p0, qa,
+                                    reinterpret_cast<unsigned short*>(xbuf + (c & 1) * W5X::PART));
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     };
 
-    if (nch > 0) stage(0);
     isr::fence_barrier_init();
     isr::tmem_fence_before_sync();
     __syncthreads();
     isr::tmem_fence_after_sync();
     const uint32_t tbase = *tslot;
-    // A K-major (bit 15 = 0), B MN-major (bit 16 = 1)
-    constexpr uint32_t idesc = isr::tc05_idesc<true>() | (1u << 16);
     bool ok = true;
-    for (int c = 0; c < nch; ++c) {
-        if (tid == 0) {
+    if (warp < W5_THREADS / 32) {
+        // staging warps: chunk c + 1 goes into buffer (c + 1) & 1 once chunk c - 1's MMAs, which
+        // read that buffer, have completed; each warp then arrives on full[(c + 1) & 1]
+        for (int c = -1; c + 1 < nch; ++c) {
+            load(c + 1);
+            if (c >= 1 && !isr::mbar_wait(isr::smem_u32(&mbar[(c + 1) & 1]), (uint32_t)((c - 1) >> 1) & 1u, 1u << 26)) {
+                ok = false;
+                break;
+            }
+            store(c + 1);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(isr::smem_u32(&full[(c + 1) & 1]));
+        }
+    } else if (lane == 0) {
+        // the issuing warp: a tcgen05.mma issue holds its thread until the tensor pipe takes it,
+        // so this thread does nothing else.  A = the activation planes, MN-major (bit 15): LBO =
+        // 128 B along K (8 positions), SBO = 16 B along M, so M-group j (rows 8 j ..) is channel
+        // group g started j rows later, i.e. tap j; B = the gradient's hi / lo rows, K-major: LBO =
+        // 128 B along K, SBO = W5_ASBO along N (8 rows).  N = 64, M = 128 (M-groups 9-15 unused).
+        constexpr uint32_t idesc =
+            (isr::tc05_idesc<true>() & ~(0x3Fu << 17)) | ((uint32_t)(2 * CH >> 3) << 17) | (1u << 15);
+        for (int c = 0; c < nch; ++c) {
+            if (!isr::mbar_wait(isr::smem_u32(&full[c & 1]), (uint32_t)(c >> 1) & 1u, 1u << 26)) {
+                ok = false;
+                break;
+            }
             isr::tmem_fence_after_sync();
-            // no swizzle: A's LBO steps along K (8 positions = 128 B) and its SBO along M (8 rows);
-            // B's LBO along K (8 positions = 128 B) and its SBO along N (8 channels = a plane).  The
-            // descriptors are built once: the start field counts 16-byte units, so K-step s adds
-            // 16 (256 B) to both and tap k adds k (one 16-byte row) to B.  Every address stays in
-            // the shared window (below 0x40000 B), so the 14-bit field never carries.
-            const uint64_t ad0 = isr::tc05_desc(isr::smem_u32(abuf + (c & 1) * W5_ABUF), 128, W5_ASBO);
-            const uint64_t bd0 = isr::tc05_desc(isr::smem_u32(xbuf + (c & 1) * W5X::PART), 128, W5X::PLANE);
+            // descriptors built once per chunk; K-step s adds 16 (256 B) to the 16-byte-unit start
+            // field of both (addresses stay below 0x40000 B: the field never carries)
+            const uint64_t bd0 = isr::tc05_desc(isr::smem_u32(abuf + (c & 1) * W5_ABUF), 128, W5_ASBO);
+            const uint32_t xa = isr::smem_u32(xbuf + (c & 1) * W5X::PART);
+            uint64_t ad0[4];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) ad0[g] = isr::tc05_desc(xa + g * W5X::PLANE, 128, 16);
 #pragma unroll 1
             for (int s = 0; s < W5_CHUNK / 16; ++s) {
-                const uint64_t ad = ad0 + 16u * (uint32_t)s, bd = bd0 + 16u * (uint32_t)s;
                 const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
 #pragma unroll
-                for (int tap = 0; tap < KT; ++tap) isr::tc05_mma(tbase + 32u * tap, ad, bd + (uint32_t)tap, idesc, acc);
+                for (int g = 0; g < 4; ++g)
+                    isr::tc05_mma(tbase + (uint32_t)(2 * CH * g), ad0[g] + 16u * (uint32_t)s, bd0 + 16u * (uint32_t)s,
+                                  idesc, acc);
             }
             isr::tc05_commit(isr::smem_u32(&mbar[c & 1]));
         }
-        if (c + 1 < nch) {
-            // the buffer of chunk c + 1 was read by chunk c - 1's MMAs
-            if (c >= 1) ok = isr::mbar_wait(isr::smem_u32(&mbar[(c + 1) & 1]), (uint32_t)((c - 1) >> 1) & 1u, 1u << 26) && ok;
-            stage(c + 1);
-        }
-        isr::tmem_fence_before_sync();
-        __syncthreads();
     }
-    // the last commit covers every MMA of this CTA
-    if (nch > 0) ok = isr::mbar_wait(isr::smem_u32(&mbar[(nch - 1) & 1]), (uint32_t)((nch - 1) >> 1) & 1u, 1u << 26) && ok;
+    // the last commit covers every MMA of this CTA; a thread whose wait ran out skips it
+    if (nch > 0 && ok) ok = isr::mbar_wait(isr::smem_u32(&mbar[(nch - 1) & 1]), (uint32_t)((nch - 1) >> 1) & 1u, 1u << 26);
+    isr::tmem_fence_before_sync();
+    ok = __syncthreads_and(ok) != 0;
     isr::tmem_fence_after_sync();
-    // epilogue: rows 0-31 (hi, lane quarter 0) and 32-63 (lo, quarter 1); warps 0-1 taps 0-4,
-    // warps 4-5 taps 5-8
-    const int quarter = warp & 3, half = warp >> 2;
-    if (nch > 0 && ok && quarter < 2) {
-        const int co = lane;
-#pragma unroll 1
-        for (int tap = half * 5; tap < (half ? KT : 5); ++tap) {
-            uint32_t r[32];
-            isr::tmem_ld32(isr::tmem_warp_lane_base(tbase) + 32u * tap, r);
-            isr::tmem_wait_ld32(r);
+    // epilogue: D_g (columns 64 g ..) row 8 t + i (TMEM lane) = tap t, input channel 8 g + i;
+    // columns 0-31 the hi and 32-63 the lo part of output channel co.  Warp w reads lane quarter
+    // w % 4 (taps 4 (w % 4) ..) of channel group g = w / 4; taps 9-15 are padding.
+    static_assert(W5_THREADS == 512, "sixteen epilogue warps: four lane quarters x four channel groups");
+    const int quarter = warp & 3, g = warp >> 2;
+    if (ok && warp < W5_THREADS / 32 && quarter < 3) {
+        const int t = 4 * quarter + (lane >> 3), ci = 8 * g + (lane & 7);
+        uint32_t rh[32], rl[32];
+        isr::tmem_ld32(isr::tmem_warp_lane_base(tbase) + (uint32_t)(2 * CH * g), rh);
+        isr::tmem_ld32(isr::tmem_warp_lane_base(tbase) + (uint32_t)(2 * CH * g + CH), rl);
+        isr::tmem_wait_ld32(rh);
+        isr::tmem_wait_ld32(rl);
+        if (t < KT) {
 #pragma unroll
-            for (int ci = 0; ci < CH; ++ci) atomicAdd(&dW[((size_t)co * CH + ci) * KT + tap], __uint_as_float(r[ci]));
+            for (int co = 0; co < CH; ++co)
+                atomicAdd(&dW[((size_t)co * CH + ci) * KT + t], __uint_as_float(rh[co]) + __uint_as_float(rl[co]));
         }
     }
     isr::tmem_fence_before_sync();
     __syncthreads();
     isr::tmem_fence_after_sync();
-    if (warp == 0) isr::tmem_dealloc(tbase, 512);
+    if (warp == 0) isr::tmem_dealloc(tbase, W5_TMEM_COLS);
     if (tid < CH) atomicAdd(&db[tid], db_s[tid]);
 }
 
@@ -1593,9 +1645,9 @@ isr_status backward_t(isr_est* e, int n, const float* fpos, const float* pres)
         } else {
             if constexpr (kTensorConv<T>) {
                 if (e->conv05) {
-                    const int span5 = W5_CHUNK * wgrad_span_chunks(L, n, e->sms);
-                    wgrad_tc05_kernel<<<dim3((L + span5 - 1) / span5, n), W5_THREADS, W5_SMEM_LAUNCH, s>>>(
-                        reinterpret_cast<const __nv_bfloat16*>(act[l - 1]), da, L, span5, e->grad + w_off(l),
+                    const int chunks = n * ((L + W5_CHUNK - 1) / W5_CHUNK);
+                    wgrad_tc05_kernel<<<std::min(chunks, e->sms), W5_BLOCK, W5_SMEM_LAUNCH, s>>>(
+                        reinterpret_cast<const __nv_bfloat16*>(act[l - 1]), da, L, n, e->grad + w_off(l),
                         e->grad + b_off(l));
                 } else {
                     wgrad_tc_kernel<<<dim3((L + span - 1) / span, n), 256, wgrad_tc_smem_bytes(), s>>>(

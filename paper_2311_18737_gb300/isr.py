@@ -103,6 +103,7 @@ class IsrPlanInfo(ctypes.Structure):
         ("kernel_launches", ctypes.c_int64),
         ("kernel_ms", ctypes.c_double),
         ("kernel_timed", ctypes.c_int64),
+        ("host_block_growth", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -45,6 +45,7 @@ int main(void)
     FIELD(isr_plan_info, kernel_launches);
     FIELD(isr_plan_info, kernel_ms);
     FIELD(isr_plan_info, kernel_timed);
+    FIELD(isr_plan_info, host_block_growth);
 
     SIZE(isr_window);
     FIELD(isr_window, echo);

@@ -173,10 +173,11 @@ def test_training_gains_over_peak_fit():
 
 @pytest.mark.parametrize("precision", ENGINES)
 def test_bf16_gradients_many_rows_several_chunks_per_cta(precision):
-    """64 rows x 1100 positions: the tcgen05 weight gradient then runs 768-position spans, three
-    256-position chunks per CTA through its double-buffered staging (two in the row's last CTA),
-    and the tcgen05 convolutions run three 256-position CTAs per row; exact (dyadic) inputs, the
-    same bound as the other BF16 gradient tests."""
+    """64 rows x 1100 positions: the tcgen05 weight gradient then spreads 320 chunks of 256
+    positions over one CTA per SM (two or three per CTA through its double-buffered staging, most
+    ranges crossing from one row into the next), and the persistent tcgen05 convolutions take
+    several 256-position tiles per CTA; exact (dyadic) inputs, the same bound as the other BF16
+    gradient tests."""
     e, theta, x, f, y, (xd, fd, yd) = _dyadic_case(B=64, L=1100, seed=9, precision=precision)
     loss, g = e.grad(xd, fd, yd)
     rl, rg = ref.loss_and_grad(theta.astype(np.float64), x, f, y, store=ref.round_bf16)
