@@ -243,6 +243,20 @@ isr_status isr_peak_fit(const float* spectra, int32_t n_ranges, int32_t nfft, in
 isr_status isr_fp32_peak(int32_t device, int32_t paired, double* tflops, double* ms);
 
 /*
+ * Measured tcgen05 tensor-pipe rate of `device` for one MMA shape: kind::f16 (BF16 operands read
+ * from shared memory, FP32 accumulator in tensor memory), M = 128, K = 16 and N = n (32, 64, 128
+ * or 256).  One thread per CTA issues 4096 MMAs back to back, one CTA per SM; 3 runs on an
+ * internal stream, the best of runs 2-3 reported.  Writes *tflops (2 FLOP per multiply-add over
+ * all SMs) and *cycles_per_mma (SM clock cycles per MMA, mean over the CTAs).  The learned
+ * estimator's convolutions issue N = 32 and N = 64 MMAs, so this is their tensor roofline.
+ * Blocking; allocates a few bytes of device memory for the duration of the call.  The paper has
+ * no counterpart.  Errors: ISR_ERR_INVALID_ARG (NULL output, n not one of the four; checked
+ * before any CUDA call), ISR_ERR_CUDA, ISR_ERR_TIMEOUT (an MMA commit did not complete within the
+ * bounded wait).
+ */
+isr_status isr_tc05_rate(int32_t device, int32_t n, double* tflops, double* cycles_per_mma);
+
+/*
  * Learned plasma-line estimator (the network maps an integrated spectrum to the line's
  * position and presence; Eq. 1 links that position to the electron density).  Network:
  * four 9-tap, 32-channel 1-D convolutions with ReLU over the band's standardised log

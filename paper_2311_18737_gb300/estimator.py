@@ -287,6 +287,14 @@ def main():
         x = torch.randn((a.bench_predict, ln), generator=g, device=est.dev)
         res = predict_rate(est, x, ln)
         res.update({"precision": a.precision, "batch": a.batch, "net_band": [lo, lo + ln]})
+        if prec == isr.ISR_EST_BF16:
+            # the forward convolutions issue M = 128, N = 32, K = 16 MMAs: their measured rate is
+            # the tensor roofline of this pass (the N = 256 rate is the part's dense BF16 peak)
+            r32, _ = isr.isr_tc05_rate(32)
+            r256, _ = isr.isr_tc05_rate(256)
+            res.update({"tc05_rate_n32_tflops": r32, "tc05_rate_n256_tflops": r256,
+                        "conv_frac_of_n32_rate": res["predict_conv_tflops"] / r32,
+                        "conv_frac_of_n256_rate": res["predict_conv_tflops"] / r256})
         print(json.dumps(res, indent=1))
         if a.out:
             with open(a.out, "w") as fh:

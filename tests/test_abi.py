@@ -80,6 +80,14 @@ def test_fp32_peak_rejects_bad_arguments_on_host():
     assert lib.isr_fp32_peak(0, 2, ctypes.byref(tf), ctypes.byref(ms)) == isr.ISR_ERR_INVALID_ARG
 
 
+def test_tc05_rate_rejects_bad_arguments_on_host():
+    lib = isr.load_library()
+    tf, cyc = ctypes.c_double(), ctypes.c_double()
+    assert lib.isr_tc05_rate(0, 32, None, None) == isr.ISR_ERR_INVALID_ARG
+    for n in (0, 16, 48, 512):
+        assert lib.isr_tc05_rate(0, n, ctypes.byref(tf), ctypes.byref(cyc)) == isr.ISR_ERR_INVALID_ARG
+
+
 def _status(fn, *args, msg=None):
     """Status of a call that must fail; msg: a fragment its error text must contain (so that
     the intended check, not an earlier one, fired)."""
