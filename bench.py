@@ -411,6 +411,12 @@ def run_ours(args):
                          if (traffic and kernel_ms > 0 and peaks.get("hbm_gbs")) else None,
                          "frac_of_measured": (achieved / measured["ffma"]) if (achieved and measured) else None},
             "clocks": clocks, "e2e": e2e}
+    if args.phase_cycles:
+        # debug build (ISR_LIBRARY=.../libisr_debug.so): SM cycles per IPP of one CTA, by phase,
+        # summed over every launch of the plan (probe, warm-up, timed steps)
+        cyc = isr.isr_plan_phase_cycles(plan.handle)
+        line["phase_cycles_per_ipp"] = {k: cyc[i] / max(1, cyc[4]) for i, k in
+                                        enumerate(("window_wait_and_barrier", "pass0", "middle_pass", "last_pass"))}
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         v, ng, dt = _cpu_sample(w, args.ref_gates, args.ref_ipps, threads)
@@ -467,6 +473,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--order", type=int, default=None, help="force a radix order (no autotuning)")
     ap.add_argument("--no-peak", action="store_true", help="skip the FP32 FMA-rate microkernel")
+    ap.add_argument("--phase-cycles", action="store_true",
+                    help="with the debug library (ISR_LIBRARY): report the fused kernel's cycles per IPP by phase")
     ap.add_argument("--precision", type=int, default=0,
                     help="first-pass engine (isr_plan_set_precision): 0 SIMT FP32; 1-4 mma.sync, 5-8 tcgen05 tensor cores")
     ap.add_argument("--ref-gates", type=int, default=256)

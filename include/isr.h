@@ -137,6 +137,16 @@ isr_status isr_plan_query(const isr_plan* plan, isr_plan_info* info);
 /* Turn per-launch CUDA-event timing of the fused kernel on (1) or off (0). */
 isr_status isr_plan_set_profiling(isr_plan* plan, int32_t enable);
 
+/* Tracing, debug build only (-DISR_DEBUG): the Stockham fused kernels (every nfft; at nfft 16384
+ * radix orders 0-2 and 6-8) time the phases of their IPP loop with the SM clock, as seen by
+ * thread 0 of each CTA, and add them up over all CTAs and launches of the plan:
+ *   out[0] waiting for the staged window + the first barrier, out[1] pass 0 (decode, first DFT,
+ *   exchange stores), out[2] the middle pass, out[3] the last pass (DFT, |X|^2 accumulation),
+ *   out[4] the IPPs those CTAs processed (so out[i] / out[4] = cycles per IPP of one CTA).
+ * Synchronises the plan's stream.  The release build records nothing and returns
+ * ISR_ERR_UNSUPPORTED.  Errors: ISR_ERR_INVALID_ARG (NULL), ISR_ERR_UNSUPPORTED, ISR_ERR_CUDA. */
+isr_status isr_plan_phase_cycles(isr_plan* plan, uint64_t out[5]);
+
 /* Bound of every wait on a staged echo window, in mbarrier polls (default 2^22, on the
  * order of a second).  A wait that runs out makes the kernel stop, record the failure
  * and return; the next isr_spectra reports ISR_ERR_TIMEOUT.  polls must be > 0. */

@@ -157,6 +157,7 @@ struct isr_plan {
     cudaEvent_t hs_free[2] = {nullptr, nullptr};
     cudaEvent_t hs_t[4] = {nullptr, nullptr, nullptr, nullptr};   // block 0: copy start / end, kernels start / end
     int64_t hs_growth = 0;    // block growth the last multi-block host-input call measured (0: none yet)
+    unsigned long long* phase = nullptr;   // debug builds: [5] phase cycles of the fused kernel
 };
 
 namespace {
@@ -234,6 +235,7 @@ isr_status launch_block(isr_plan* p, const uint32_t* echo, const char* tx, int64
         a.chunk_len = (int)chunk;
         a.wait_limit = p->wait_limit;
         a.drop_ipp = (p->drop_ipp >= done && p->drop_ipp < done + n_l) ? (int)(p->drop_ipp - done) : -1;
+        a.phase_cycles = p->phase;
 
         std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
         if (p->prof) {
@@ -420,6 +422,10 @@ isr_status isr_plan_create(isr_plan** out, const isr_plan_desc* desc)
     e = cudaMalloc(&p->acc, (size_t)(RN * 8));
     if (e == cudaSuccess) e = cudaMalloc(&p->partial, (size_t)(mc * RN * 4));
     if (e == cudaSuccess) e = cudaMalloc(&p->status, sizeof(int));
+#ifdef ISR_DEBUG
+    if (e == cudaSuccess) e = cudaMalloc(&p->phase, 5 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->phase, 0, 5 * sizeof(unsigned long long), p->stream);
+#endif
     if (e != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(e == cudaErrorMemoryAllocation ? ISR_ERR_NO_MEMORY : ISR_ERR_CUDA, "device allocation failed: %s",
@@ -533,6 +539,18 @@ isr_status isr_plan_set_profiling(isr_plan* p, int32_t enable)
 {
     if (!p) return fail(ISR_ERR_INVALID_ARG, "plan is NULL");
     p->prof = enable != 0;
+    return ISR_OK;
+}
+
+isr_status isr_plan_phase_cycles(isr_plan* p, uint64_t* out)
+{
+    if (!p || !out) return fail(ISR_ERR_INVALID_ARG, "plan or out is NULL");
+    if (!p->phase) return fail(ISR_ERR_UNSUPPORTED, "phase cycles are recorded by the debug build only (-DISR_DEBUG)");
+    DeviceGuard guard(p->dev);
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    unsigned long long h[5];
+    CUDA_TRY(cudaMemcpy(h, p->phase, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 5; ++i) out[i] = (uint64_t)h[i];
     return ISR_OK;
 }
 
@@ -756,6 +774,7 @@ void isr_destroy(isr_plan* p)
     cudaFree(p->acc);
     cudaFree(p->partial);
     cudaFree(p->status);
+    cudaFree(p->phase);
     cudaFree(p->out_stage);
     cudaGetLastError();
     delete p;

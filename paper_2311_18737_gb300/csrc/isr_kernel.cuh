@@ -161,6 +161,9 @@ struct KArgs {
     int chunk_len;          // IPPs per chunk (blockIdx.y)
     unsigned wait_limit;    // try_wait polls before giving up
     int drop_ipp;           // test hook: never stage this IPP (launch-relative), -1 = off
+    // debug builds: [5] = SM cycles of the IPP loop's phases summed over CTAs as seen by thread 0
+    // (window wait + barrier, pass 0, middle pass, last pass) and the IPPs counted; NULL = off
+    unsigned long long* phase_cycles = nullptr;
 };
 
 // ---------------------------------------------------------------- async-copy primitives
@@ -587,7 +590,14 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
     float2 v[E];
     bool timed_out = false;
     int it = 0;
+#ifdef ISR_DEBUG
+    long long ph[4] = {0, 0, 0, 0}, tq0 = 0, tq1 = 0, tq2 = 0;   // phase cycles (thread 0 reports)
+#endif
     for (int p = p_begin; p < p_end; ++p, ++it) {
+#ifdef ISR_DEBUG
+        const long long tq = clock64();
+        if (p > p_begin) ph[3] += tq - tq2;
+#endif
         bool ok = mbar_wait(bar, (phase0 + (uint32_t)it) & 1u, a.wait_limit);
         // every thread of the gate agrees before anyone leaves; this barrier also orders the
         // previous IPP's last-pass reads of xch before this IPP's first-pass writes
@@ -598,6 +608,10 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
                 break;
             }
         }
+#ifdef ISR_DEBUG
+        tq0 = clock64();
+        ph[0] += tq0 - tq;
+#endif
         const char* txrow = txbase + (size_t)p * (size_t)a.tx_stride * CHIP;
         if constexpr (p0_is_mmasync(P0)) {
             if (a.tx_stride != 0) signs = tc_load_signs(reinterpret_cast<const int8_t*>(txrow));
@@ -657,6 +671,11 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
             fence_proxy_async();
             issue(p + 1);
         }
+#ifdef ISR_DEBUG
+        tq1 = clock64();
+        ph[1] += tq1 - tq0;
+        tq2 = tq1;
+#endif
         if constexpr (NP == 1) continue;
 
         // ---- middle pass (three-pass sizes), in place: butterfly j reads x[j + (N/R) k] and
@@ -701,6 +720,10 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
             gsync();
         }
 
+#ifdef ISR_DEBUG
+        tq2 = clock64();
+        ph[2] += tq2 - tq1;
+#endif
         // ---- last pass: read, twiddle, DFT, accumulate |X|^2 in registers
         {
             constexpr int R = RL;
@@ -732,6 +755,13 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
         }
     }
 
+#ifdef ISR_DEBUG
+    if (!timed_out && a.phase_cycles && threadIdx.x == 0 && p_end > p_begin) {
+        ph[3] += clock64() - tq2;
+        for (int i = 0; i < 4; ++i) atomicAdd(a.phase_cycles + i, (unsigned long long)ph[i]);
+        atomicAdd(a.phase_cycles + 4, (unsigned long long)(p_end - p_begin));
+    }
+#endif
     if (timed_out) {
         if (t == 0) atomicOr(a.status, 1);
         // let the copy still in flight land before the CTA's shared memory is released

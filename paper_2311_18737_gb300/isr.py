@@ -36,7 +36,7 @@ STATUS_NAMES = {0: "ISR_OK", 1: "ISR_ERR_INVALID_ARG", 2: "ISR_ERR_UNSUPPORTED",
 # every entry point declared in include/isr.h
 EXPORTS = ("isr_plan_create", "isr_integrate", "isr_spectra", "isr_plan_query", "isr_plan_set_profiling",
            "isr_plan_set_wait_limit", "isr_plan_set_order", "isr_plan_set_precision", "isr_plan_test_drop_window", "isr_destroy", "isr_last_error",
-           "isr_integrate_static", "isr_peak_fit", "isr_fp32_peak", "isr_tc05_rate", "isr_est_create", "isr_est_set_params", "isr_est_get_params",
+           "isr_integrate_static", "isr_peak_fit", "isr_fp32_peak", "isr_tc05_rate", "isr_plan_phase_cycles", "isr_est_create", "isr_est_set_params", "isr_est_get_params",
            "isr_est_features", "isr_est_grad", "isr_est_train_step", "isr_est_predict", "isr_est_destroy",
            "isr_batch_create", "isr_batch_run", "isr_batch_wait", "isr_batch_query", "isr_batch_destroy")
 
@@ -177,6 +177,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                   ctypes.POINTER(ctypes.c_double)]
     lib.isr_tc05_rate.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double)]
+    lib.isr_plan_phase_cycles.argtypes = [P, P]
     lib.isr_est_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_int32, ctypes.c_int32, P]
     lib.isr_est_set_params.argtypes = [P, P]
@@ -300,6 +301,14 @@ def isr_fp32_peak(device: int = 0, paired: bool = False) -> tuple:
     _check(load_library().isr_fp32_peak(int(device), int(bool(paired)), ctypes.byref(tf), ctypes.byref(ms)),
            "isr_fp32_peak")
     return tf.value, ms.value
+
+
+def isr_plan_phase_cycles(plan) -> list:
+    """Debug build only: summed SM cycles of the fused kernel's IPP-loop phases (window wait,
+    pass 0, middle pass, last pass) as seen by thread 0 of each CTA, and the IPPs counted."""
+    out = (ctypes.c_uint64 * 5)()
+    _check(load_library().isr_plan_phase_cycles(plan, out), "isr_plan_phase_cycles")
+    return [int(v) for v in out]
 
 
 def isr_tc05_rate(n: int, device: int = 0) -> tuple:

@@ -80,6 +80,11 @@ def test_fp32_peak_rejects_bad_arguments_on_host():
     assert lib.isr_fp32_peak(0, 2, ctypes.byref(tf), ctypes.byref(ms)) == isr.ISR_ERR_INVALID_ARG
 
 
+def test_phase_cycles_rejects_null_on_host():
+    lib = isr.load_library()
+    assert lib.isr_plan_phase_cycles(None, None) == isr.ISR_ERR_INVALID_ARG
+
+
 def test_tc05_rate_rejects_bad_arguments_on_host():
     lib = isr.load_library()
     tf, cyc = ctypes.c_double(), ctypes.c_double()

@@ -5,7 +5,9 @@ the copy, and reports a failed check as ISR_ERR_OUT_OF_RANGE (never a trap or a 
 * CPU: the debug library compiles for sm_103a and exports every declared entry point.
 * GPU: with valid inputs only, the debug build gives the same spectra as the oracle for
   every kernel family (several gates per warp, per-gate named barriers, one gate per CTA in
-  each radix order), i.e. no check fires on a valid geometry.
+  each radix order), i.e. no check fires on a valid geometry; its phase-cycle tracing
+  (isr_plan_phase_cycles) reports every phase of the Stockham kernels, and the release build
+  refuses the call.
 """
 import ctypes
 import os
@@ -48,6 +50,15 @@ for nfft, n_ranges, order in cases:
         plan.integrate(torch.from_numpy(echo).to(dev), torch.from_numpy(code).to(dev), w.n_ipp)
         out = torch.empty((n_ranges, nfft), dtype=torch.float32, device=dev)
         plan.spectra(out)
+        cyc = isr.isr_plan_phase_cycles(plan.handle)
+    # the Stockham kernels record their phases (thread 0 of each CTA); the warp-local and paired
+    # orders do not
+    stockham = order in (0, 1, 2) or nfft < 16384
+    if stockham:
+        assert cyc[4] > 0 and min(cyc[:2]) > 0 and cyc[3] > 0, (nfft, order, cyc)
+        assert sum(cyc[:4]) / cyc[4] < 1e7, (nfft, order, cyc)   # cycles per IPP and CTA, sane
+    else:
+        assert cyc == [0, 0, 0, 0, 0], (nfft, order, cyc)
     assert_parity(out.cpu().numpy().astype(np.float64), ref, rtol=RTOL, what=f"debug build nfft {nfft} order {order}")
 print("debug build parity ok")
 """
@@ -61,3 +72,11 @@ def test_debug_build_parity_on_valid_inputs():
     r = subprocess.run([sys.executable, "-c", CHILD], capture_output=True, text=True, env=env, timeout=900, cwd=ROOT)
     assert r.returncode == 0, f"debug-build child failed:\n{r.stdout[-2000:]}\n{r.stderr[-4000:]}"
     assert "debug build parity ok" in r.stdout
+
+
+@pytest.mark.gpu
+def test_release_build_refuses_phase_cycles():
+    torch = pytest.importorskip("torch")
+    with isr.Plan(nfft=256, n_ranges=4, echo_stride=384, range_step=25, tx_type=isr.ISR_TX_PM1, device=0) as plan:
+        out = (ctypes.c_uint64 * 5)()
+        assert isr.load_library().isr_plan_phase_cycles(plan.handle, out) == isr.ISR_ERR_UNSUPPORTED
