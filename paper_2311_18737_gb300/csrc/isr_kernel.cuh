@@ -223,15 +223,26 @@ __device__ __forceinline__ float2 iq_of(uint32_t w)
 template <int TXT>
 __device__ __forceinline__ float2 decode(uint32_t w, const void* txrow, int pos, uint32_t sbit)
 {
-    float2 m = iq_of(w);
     if constexpr (TXT == TX_PM1) {
-        // sbit holds the chip's sign in bit 31: flip both components' sign bits
-        return make_float2(__int_as_float(__float_as_int(m.x) ^ sbit), __int_as_float(__float_as_int(m.y) ^ sbit));
+        // sbit holds the chip's sign in bit 31.  Exact int16 -> float conversion on the integer
+        // and FMA pipes (the conversion instruction runs on a narrower pipe, and every sample of
+        // the first pass needs two): XOR 0x8000 turns each int16 into the offset-binary
+        // u = v + 2^15 in [0, 2^16); placed in the low mantissa bits of 1.5 * 2^23 it gives the
+        // float 1.5 * 2^23 + u exactly, and adding -(1.5 * 2^23 + 2^15) leaves v (all integers
+        // below 2^24).  The chip's sign goes into both magic constants, so the sum is +-v.
+        const uint32_t cs = 0x4B400000u ^ sbit;       //  1.5 * 2^23, with the chip's sign
+        const uint32_t ks = 0xCB408000u ^ sbit;       // -(1.5 * 2^23 + 2^15), with the chip's sign
+        const uint32_t wb = w ^ 0x80008000u;
+        const float fi = __int_as_float(__byte_perm(wb, cs, 0x7610));   // bytes wb.0, wb.1, cs.2, cs.3
+        const float fq = __int_as_float(__byte_perm(wb, cs, 0x7632));   // bytes wb.2, wb.3, cs.2, cs.3
+        return make_float2(fi + __int_as_float(ks), fq + __int_as_float(ks));
     } else if constexpr (TXT == TX_CI16) {
+        float2 m = iq_of(w);
         float2 e = iq_of(__ldg(reinterpret_cast<const uint32_t*>(txrow) + pos));
         // conj(e) * m = (ex mx + ey my) + i (ex my - ey mx)
         return make_float2(fmaf(e.x, m.x, e.y * m.y), fmaf(e.x, m.y, -e.y * m.x));
     } else {
+        float2 m = iq_of(w);
         float2 e = __ldg(reinterpret_cast<const float2*>(txrow) + pos);
         return make_float2(fmaf(e.x, m.x, e.y * m.y), fmaf(e.x, m.y, -e.y * m.x));
     }
