@@ -220,13 +220,21 @@ __device__ __forceinline__ float2 iq_of(uint32_t w)
     return make_float2((float)(int16_t)(w & 0xffffu), (float)(int16_t)(w >> 16));
 }
 
-template <int TXT>
+// Binary-phase codes: CVT picks how a sample's int16 pair becomes floats.  The first passes decode
+// even samples with the conversion instruction and odd ones with the magic-number form below, so
+// that both pipes share the work: at nfft 16384 either form alone took 320-323 ms per
+// integration of the realistic workload (order 6), the split 312.5 ms.
+template <int TXT, bool CVT = false>
 __device__ __forceinline__ float2 decode(uint32_t w, const void* txrow, int pos, uint32_t sbit)
 {
-    if constexpr (TXT == TX_PM1) {
+    if constexpr (TXT == TX_PM1 && CVT) {
+        // the conversion instruction, then sbit (the chip's sign in bit 31) flips both signs
+        const float2 m = iq_of(w);
+        return make_float2(__int_as_float(__float_as_int(m.x) ^ sbit), __int_as_float(__float_as_int(m.y) ^ sbit));
+    } else if constexpr (TXT == TX_PM1) {
         // sbit holds the chip's sign in bit 31.  Exact int16 -> float conversion on the integer
-        // and FMA pipes (the conversion instruction runs on a narrower pipe, and every sample of
-        // the first pass needs two): XOR 0x8000 turns each int16 into the offset-binary
+        // and FMA pipes (the conversion instruction runs on a narrower pipe): XOR 0x8000 turns
+        // each int16 into the offset-binary
         // u = v + 2^15 in [0, 2^16); placed in the low mantissa bits of 1.5 * 2^23 it gives the
         // float 1.5 * 2^23 + u exactly, and adding -(1.5 * 2^23 + 2^15) leaves v (all integers
         // below 2^24).  The chip's sign goes into both magic constants, so the sum is +-v.
@@ -653,7 +661,7 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
                 // chips at or past code_len are the zero padding (and are never read)
                 u[k] = make_float2(0.f, 0.f);
                 if (FULL || pos < a.code_len)
-                    u[k] = decode<TXT>(stage[off + pos], txrow, pos, (signs << (31 - (b * R0 + k))) & 0x80000000u);
+                    u[k] = decode<TXT, (k & 1) == 0>(stage[off + pos], txrow, pos, (signs << (31 - (b * R0 + k))) & 0x80000000u);
             });
             unit_dft<R0, LOG2N>(u);
             if constexpr (NP == 1) {
@@ -957,7 +965,7 @@ __device__ __forceinline__ bool integrate_unit_wl(A a, const int gx, const int c
                 const int pos = n + 1024 * k;
                 u[k] = make_float2(0.f, 0.f);
                 if (FULL || pos < a.code_len)
-                    u[k] = decode<TXT>(stage[off + pos], txrow, pos, (signs << (31 - (b * M + k))) & 0x80000000u);
+                    u[k] = decode<TXT, (k & 1) == 0>(stage[off + pos], txrow, pos, (signs << (31 - (b * M + k))) & 0x80000000u);
             });
             sdft<M>(u);
             if constexpr (TMT) {
