@@ -196,10 +196,10 @@ def _cpu_sample(w, n_gates, n_ipp, threads):
     sel = np.unique(np.linspace(0, w.n_ranges - 1, n_gates).astype(np.int32))
     oracle.build()
     t0 = time.perf_counter()
-    oracle.integrate(echo, code, nfft=w.nfft, n_ranges=w.n_ranges, range_start=w.range_start,
-                     range_step=w.range_step, sel=sel, n_threads=threads)
+    ref = oracle.integrate(echo, code, nfft=w.nfft, n_ranges=w.n_ranges, range_start=w.range_start,
+                           range_step=w.range_step, sel=sel, n_threads=threads)
     dt = time.perf_counter() - t0
-    return len(sel) * n_ipp / dt, len(sel), dt
+    return len(sel) * n_ipp / dt, len(sel), dt, ref, sel
 
 
 def _numpy_sample(w, n_gates, n_ipp):
@@ -228,7 +228,7 @@ def run_reference(args):
         _cpu_sample(w, gates, ipps, threads)
     rates, secs = [], 0.0
     for _ in range(args.steps):
-        r, ng, dt = _cpu_sample(w, gates, ipps, threads)
+        r, ng, dt = _cpu_sample(w, gates, ipps, threads)[:3]
         rates.append(r)
         secs += dt
     value = len(rates) * ng * ipps / secs
@@ -419,10 +419,17 @@ def run_ours(args):
                                         enumerate(("window_wait_and_barrier", "pass0", "middle_pass", "last_pass"))}
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        v, ng, dt = _cpu_sample(w, args.ref_gates, args.ref_ipps, threads)
+        v, ng, dt, ref, sel = _cpu_sample(w, args.ref_gates, args.ref_ipps, threads)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"{ng} gates spread over the workload x the first {args.ref_ipps} IPPs "
                                           f"({dt:.1f} s wall)"}
+        # the library on the same sample (same echo rows, all gates, then the sampled rows):
+        # the largest per-bin relative difference from the FP64 oracle
+        import numpy as np
+        plan.integrate(echo[:args.ref_ipps], code_d, args.ref_ipps)
+        plan.spectra(out, isr.ISR_RESET_AFTER)
+        got = out[torch.as_tensor(sel, dtype=torch.long, device=out.device)].double().cpu().numpy()
+        line["cpu_baseline"]["max_rel_err_vs_oracle"] = float(np.max(np.abs(got - ref) / ref))
         v, ng, dt = _numpy_sample(w, 64, 32)
         line["cpu_baseline_numpy"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "paper-style NumPy (Sec. 3.3)",
                                       "sample": f"{ng} gates spread over the workload x the first 32 IPPs "
