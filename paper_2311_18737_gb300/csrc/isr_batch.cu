@@ -64,7 +64,10 @@ __device__ __noinline__ bool run_unit(const BatchWin& w, const BatchUnit& u, uns
                                                              setup);
     } else {
         using S = isr::Sched<L, O>;
-        return isr::integrate_unit<L, isr::TX_PM1, O, false, isr::P0_SIMT, const isr::KArgs&>(w.a, u.gx, u.cy, smem, s_phase[threadIdx.x / S::T], setup);
+        // every sample on the conversion instruction: the persistent kernel holds all window
+        // shapes at the 128-register cap, where the split decode measured slower
+        return isr::integrate_unit<L, isr::TX_PM1, O, false, isr::P0_SIMT, const isr::KArgs&, false, false>(
+            w.a, u.gx, u.cy, smem, s_phase[threadIdx.x / S::T], setup);
     }
 }
 

@@ -450,8 +450,10 @@ __device__ __forceinline__ bool debug_window_ok(const A& a, int64_t s_r, int off
 // reference to a shared-memory copy, read where needed rather than held in registers.
 // TMT: twiddles of passes 1 and 2 from tensor memory at tmem (the CTA's allocation of
 // Sched::TM_COLS columns); setup writes them.
+// SPLITDEC: binary-phase samples of the first pass decoded half with the conversion instruction,
+// half in the magic-number form (see decode); false: all with the conversion instruction.
 template <int LOG2N, int TXT, int ORDER = 0, bool FULL = false, int P0 = P0_SIMT, class A = const KArgs,
-          bool TMT = false>
+          bool TMT = false, bool SPLITDEC = true>
 __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, unsigned char* smem,
                                                const uint32_t phase0, const bool setup, const uint32_t tmem = 0)
 {
@@ -661,7 +663,8 @@ __device__ __forceinline__ bool integrate_unit(A a, const int gx, const int c, u
                 // chips at or past code_len are the zero padding (and are never read)
                 u[k] = make_float2(0.f, 0.f);
                 if (FULL || pos < a.code_len)
-                    u[k] = decode<TXT, (k & 1) == 0>(stage[off + pos], txrow, pos, (signs << (31 - (b * R0 + k))) & 0x80000000u);
+                    u[k] = decode<TXT, SPLITDEC ? (k & 1) == 0 : true>(stage[off + pos], txrow, pos,
+                                                                       (signs << (31 - (b * R0 + k))) & 0x80000000u);
             });
             unit_dft<R0, LOG2N>(u);
             if constexpr (NP == 1) {
