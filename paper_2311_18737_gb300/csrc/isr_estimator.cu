@@ -1124,6 +1124,87 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const TH* __restrict__ h, co
     }
 }
 
+// Weight gradient of the one-channel first layer:
+//   dW1[co][k] += sum_i da[b][co][i] x[b][i + k - 4],  db1[co] += sum_i da[b][co][i]
+// The n_rows x ceil(L / W1_SPAN) spans, row after row, are split into gridDim.x contiguous ranges
+// (two CTAs per SM: at 128 rows x 4608 positions 45.5 us per launch, against 49.5 us with one and
+// 64.6 us with four, where most CTAs take one span), and a CTA keeps its sums in registers over
+// its spans, so every weight receives one atomic per CTA, not one per span.  Within a span [i0, i0 + W1_SPAN) of row b warp w
+// takes output channels 4 w .. 4 w + 3 and lane l the positions i0 + l + 32 m, so every gradient
+// row is read coalesced straight from global memory and the input row once from shared memory;
+// the sums are reduced across lanes with shuffles at the end.
+constexpr int W1_SPAN = 1024;   // a multiple of 32 x 8 (the step)
+
+template <class TH>
+__global__ void __launch_bounds__(256) wgrad1_kernel(const TH* __restrict__ x, const float* __restrict__ da, int L,
+                                                     int n_rows, float* __restrict__ dW, float* __restrict__ db)
+{
+    constexpr int CPW = CH / 8;   // output channels per warp
+    __shared__ float xs[W1_SPAN + KT - 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int spr = (L + W1_SPAN - 1) / W1_SPAN;                 // spans per row
+    const int64_t total = (int64_t)n_rows * spr;
+    const int q_begin = (int)((int64_t)blockIdx.x * total / gridDim.x);
+    const int q_end = (int)((int64_t)(blockIdx.x + 1) * total / gridDim.x);
+    float acc[CPW][KT], dbacc[CPW];
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+        dbacc[c] = 0.f;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) acc[c][k] = 0.f;
+    }
+    for (int q = q_begin; q < q_end; ++q) {
+    const int b = q / spr, i0 = (q - b * spr) * W1_SPAN, iend = min(L, i0 + W1_SPAN);
+    __syncthreads();   // the previous span's reads of xs are done
+    for (int j = threadIdx.x; j < W1_SPAN + KT - 1; j += 256) {
+        const int pos = i0 - HALF + j;
+        xs[j] = (pos >= 0 && pos < L) ? ld<TH>(x, (size_t)b * L + pos) : 0.f;
+    }
+    __syncthreads();
+    const float* dar = da + ((size_t)b * CH + warp * CPW) * L;
+    // eight positions per lane and step: all 32 gradient loads of a step are in flight together
+    constexpr int U = 8;
+    for (int base = i0; base < iend; base += 32 * U) {
+        float d[CPW][U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = base + lane + 32 * u;
+#pragma unroll
+            for (int c = 0; c < CPW; ++c) d[c][u] = i < iend ? __ldg(dar + (size_t)c * L + i) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = base - i0 + lane + 32 * u;   // zero gradient past iend: no effect
+            float xv[KT];
+#pragma unroll
+            for (int k = 0; k < KT; ++k) xv[k] = xs[j + k];
+#pragma unroll
+            for (int c = 0; c < CPW; ++c) {
+                dbacc[c] += d[c][u];
+#pragma unroll
+                for (int k = 0; k < KT; ++k) acc[c][k] = fmaf(d[c][u], xv[k], acc[c][k]);
+            }
+        }
+    }
+    }
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+#pragma unroll
+        for (int k = 0; k < KT; ++k)
+            for (int o = 16; o; o >>= 1) acc[c][k] += __shfl_down_sync(0xffffffffu, acc[c][k], o);
+        for (int o = 16; o; o >>= 1) dbacc[c] += __shfl_down_sync(0xffffffffu, dbacc[c], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) {
+            const int co = warp * CPW + c;
+#pragma unroll
+            for (int k = 0; k < KT; ++k) atomicAdd(&dW[co * KT + k], acc[c][k]);
+            atomicAdd(&db[co], dbacc[c]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- first layer (one input channel)
 // h1[b][co][i] = relu(b1[co] + sum_k W1[co][k] x[b][i + k - 4]).  A thread takes two adjacent
 // positions and loops over the channels, so every channel row is written in coalesced pairs.
@@ -1641,7 +1722,9 @@ isr_status backward_t(isr_est* e, int n, const float* fpos, const float* pres)
     const int span = TC_CT * wgrad_span_chunks(L, n, std::max(1, e->wgrad_slots));
     for (int l = 4; l >= 1; --l) {
         if (l == 1) {
-            wgrad_kernel<T, 1><<<gw, 256, 0, s>>>(act[0], da, L, e->grad + OFF_W1, e->grad + OFF_B1);
+            const int spans = n * ((L + W1_SPAN - 1) / W1_SPAN);
+            wgrad1_kernel<T><<<std::min(spans, 2 * std::max(1, e->sms)), 256, 0, s>>>(act[0], da, L, n,
+                                                                                     e->grad + OFF_W1, e->grad + OFF_B1);
         } else {
             if constexpr (kTensorConv<T>) {
                 if (e->conv05) {
@@ -1763,13 +1846,13 @@ isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t 
             isr_est_destroy(e);
             return st;
         }
-        if (bf16) {
-            int sms = 0, occ = 0;
-            r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (r == cudaSuccess)
-                r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wgrad_tc_kernel, 256, wgrad_tc_smem_bytes());
-            e->wgrad_slots = std::max(1, occ) * std::max(1, sms);
-            e->sms = std::max(1, sms);
+        int sms = 0;
+        r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e->sms = std::max(1, sms);
+        if (bf16 && r == cudaSuccess) {
+            int occ = 0;
+            r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wgrad_tc_kernel, 256, wgrad_tc_smem_bytes());
+            e->wgrad_slots = std::max(1, occ) * e->sms;
             // two CTAs per SM, the shape the kernel is built for (__launch_bounds__ minimum): 128
             // registers x 256 threads, at most 86 KB of shared memory and 128 TMEM columns each
             e->c5_slots[0] = e->c5_slots[1] = C5_CTAS_PER_SM * e->sms;
