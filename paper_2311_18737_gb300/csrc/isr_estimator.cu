@@ -1541,11 +1541,19 @@ __global__ void __launch_bounds__(256) head_bwd_chunk_kernel(const T* __restrict
     const float* zb = z + (size_t)b * L;
     const T* hb = h4 + ((size_t)b * CH + warp * 4) * L;
     float* ob = da4 + ((size_t)b * CH + warp * 4) * L;
-    float dw5[4] = {0.f, 0.f, 0.f, 0.f}, db5 = 0.f;
-    for (int i = i0 + lane; i < iend; i += 32) {
+    // dL/dz once per position (every warp needs it for its four channels)
+    __shared__ float dz_s[HD_CT];
+    float db5 = 0.f;
+    for (int i = i0 + threadIdx.x; i < iend; i += 256) {
         const float d = (i - f) / SIGMA_T;
         const float dz = ys != 0.f ? ys * (__expf(zb[i] - lse) - __expf(-0.5f * d * d) * inv_st) : 0.f;
+        dz_s[i - i0] = dz;
         db5 += dz;
+    }
+    __syncthreads();
+    float dw5[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = i0 + lane; i < iend; i += 32) {
+        const float dz = dz_s[i - i0];
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
             const float hv = ld<T>(hb, (size_t)cc * L + i);
@@ -1562,7 +1570,7 @@ __global__ void __launch_bounds__(256) head_bwd_chunk_kernel(const T* __restrict
     if (lane == 0) {
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) atomicAdd(&grad[OFF_W5 + warp * 4 + cc], dw5[cc]);
-        if (warp == 0) atomicAdd(&grad[OFF_B5], db5);
+        atomicAdd(&grad[OFF_B5], db5);   // this warp's positions of the chunk
     }
 }
 
