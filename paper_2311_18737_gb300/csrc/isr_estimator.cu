@@ -483,17 +483,28 @@ __device__ __forceinline__ void c5_act_store(const unsigned short* __restrict__ 
     using G = C5<TPC>;
     constexpr int XW = G::XW, THREADS = NT, P = G::PLANE;
     constexpr int NITEM = C5Act<TPC, NT>::NITEM, PER = C5Act<TPC, NT>::PER;
+    static_assert(NITEM % 32 == 0 && THREADS % 32 == 0, "whole warps per item round (the shuffles)");
     if ((L & 7) == 0) {
+        // lane = channel c; lanes c, c ^ 1 swap halves of their 8 positions, so that the even lane
+        // holds positions 0-3 and the odd lane positions 4-7 of both channels and writes one 32-bit
+        // word (channels c & ~1, c | 1) per position: per store the even lanes fill rows j (16
+        // banks over the four planes) and the odd lanes rows j + 4 (the other 16)
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int e = threadIdx.x + u * THREADS;
             if (e >= NITEM) break;
-            const int c = e & (CH - 1), v = e / CH;
-            const uint32_t w[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+            const int c = e & (CH - 1), v = e / CH, odd = c & 1;
+            const uint32_t r0 = __shfl_xor_sync(0xffffffffu, odd ? q[u].x : q[u].z, 1);
+            const uint32_t r1 = __shfl_xor_sync(0xffffffffu, odd ? q[u].y : q[u].w, 1);
+            const uint32_t m0 = odd ? q[u].z : q[u].x, m1 = odd ? q[u].w : q[u].y;
+            const uint32_t e0 = odd ? r0 : m0, o0 = odd ? m0 : r0;   // even / odd channel, positions 0-1 of the half
+            const uint32_t e1 = odd ? r1 : m1, o1 = odd ? m1 : r1;   // positions 2-3
+            const uint32_t w[4] = {__byte_perm(e0, o0, 0x5410), __byte_perm(e0, o0, 0x7632),
+                                   __byte_perm(e1, o1, 0x5410), __byte_perm(e1, o1, 0x7632)};
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int j = 8 * v - HALF + k;
-                if (j >= 0 && j < XW) xs[c5_idx<P>(j, c)] = (unsigned short)(w[k >> 1] >> (16 * (k & 1)));
+            for (int k = 0; k < 4; ++k) {
+                const int j = 8 * v - HALF + 4 * odd + k;
+                if (j >= 0 && j < XW) *reinterpret_cast<uint32_t*>(xs + c5_idx<P>(j, c & ~1)) = w[k];
             }
         }
     } else {
@@ -553,22 +564,29 @@ __device__ __forceinline__ void c5_split_store(const float4 (&q)[C5Split<TPC>::P
 {
     constexpr int NITEM = C5Split<TPC>::NITEM, PER = C5Split<TPC>::PER, THREADS = C5<TPC>::THREADS;
     constexpr int P = C5<TPC>::PLANE;
+    static_assert(NITEM % 32 == 0 && THREADS % 32 == 0, "whole warps per item round (the shuffles)");
+    static_assert((C5<TPC>::PART / 4) % 32 == 16, "the hi and lo parts 16 banks apart");
+    // lane = channel c; lanes c, c ^ 1 swap parts: the even lane gets the hi words of both
+    // channels and the odd lane the lo words, and each writes one 32-bit word (channels c & ~1,
+    // c | 1) per position, so every store fills rows j of both parts, 32 distinct banks
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int e = threadIdx.x + u * THREADS;
         if (e >= NITEM) break;
-        const int c = e & (CH - 1), v = e / CH;
-        const float t[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+        const int c = e & (CH - 1), v = e / CH, odd = c & 1;
+        uint32_t hi0, lo0, hi1, lo1;
+        isr::split2<true>(q[u].x, q[u].y, hi0, lo0);
+        isr::split2<true>(q[u].z, q[u].w, hi1, lo1);
+        const uint32_t r0 = __shfl_xor_sync(0xffffffffu, odd ? hi0 : lo0, 1);
+        const uint32_t r1 = __shfl_xor_sync(0xffffffffu, odd ? hi1 : lo1, 1);
+        const uint32_t m0 = odd ? lo0 : hi0, m1 = odd ? lo1 : hi1;
+        const uint32_t e0 = odd ? r0 : m0, o0 = odd ? m0 : r0;   // even / odd channel, positions 0-1
+        const uint32_t e1 = odd ? r1 : m1, o1 = odd ? m1 : r1;   // positions 2-3
+        const uint32_t w[4] = {__byte_perm(e0, o0, 0x5410), __byte_perm(e0, o0, 0x7632),
+                               __byte_perm(e1, o1, 0x5410), __byte_perm(e1, o1, 0x7632)};
+        unsigned short* x = odd ? xl : xh;
 #pragma unroll
-        for (int k = 0; k < 4; k += 2) {
-            uint32_t hi, lo;
-            isr::split2<true>(t[k], t[k + 1], hi, lo);
-            const int j = 4 * v + k;
-            xh[c5_idx<P>(j, c)] = (unsigned short)(hi & 0xffffu);
-            xh[c5_idx<P>(j + 1, c)] = (unsigned short)(hi >> 16);
-            xl[c5_idx<P>(j, c)] = (unsigned short)(lo & 0xffffu);
-            xl[c5_idx<P>(j + 1, c)] = (unsigned short)(lo >> 16);
-        }
+        for (int k = 0; k < 4; ++k) *reinterpret_cast<uint32_t*>(x + c5_idx<P>(4 * v + k, c & ~1)) = w[k];
     }
 }
 
@@ -935,6 +953,8 @@ __global__ void __launch_bounds__(W5_BLOCK, 1) wgrad_tc05_kernel(const __nv_bflo
     constexpr int NITEM = CH * (W5_CHUNK / 8), PER = NITEM / W5_THREADS;
     float4 q0[PER], q1[PER];
     uint4 qa[C5Act<2, W5_THREADS>::PER];
+    float dbacc = 0.f;   // bias gradient of channel `lane` (every item of this thread has co = lane)
+    static_assert(W5_THREADS % CH == 0, "item e = tid + u W5_THREADS keeps channel e % 32 = lane");
     auto load = [&](int c) {
         const int q = q_begin + c, b = q / cpr, p0 = (q - b * cpr) * W5_CHUNK;
         const int span_end = min(L, p0 + W5_CHUNK);
@@ -971,8 +991,7 @@ __global__ void __launch_bounds__(W5_BLOCK, 1) wgrad_tc05_kernel(const __nv_bflo
             const uint32_t o = (uint32_t)((co >> 3) * W5_ASBO + kb * 128 + (co & 7) * 16);
             *reinterpret_cast<uint4*>(a + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
             *reinterpret_cast<uint4*>(a + o + 4 * W5_ASBO) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-            // bias gradient (lane = channel: 32 distinct shared addresses per warp)
-            atomicAdd(&db_s[co], ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7])));
+            dbacc += ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
         }
         c5_act_store<2, W5_THREADS>(reinterpret_cast<const unsigned short*>(h) + (size_t)b * CH * L, L, p0, qa,
                                     reinterpret_cast<unsigned short*>(xbuf + (c & 1) * W5X::PART));
@@ -1030,6 +1049,7 @@ __global__ void __launch_bounds__(W5_BLOCK, 1) wgrad_tc05_kernel(const __nv_bflo
             isr::tc05_commit(isr::smem_u32(&mbar[c & 1]));
         }
     }
+    if (warp < W5_THREADS / 32) atomicAdd(&db_s[lane], dbacc);
     // the last commit covers every MMA of this CTA; a thread whose wait ran out skips it
     if (nch > 0 && ok) ok = isr::mbar_wait(isr::smem_u32(&mbar[(nch - 1) & 1]), (uint32_t)((nch - 1) >> 1) & 1u, 1u << 26);
     isr::tmem_fence_before_sync();
