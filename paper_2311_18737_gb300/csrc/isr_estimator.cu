@@ -51,6 +51,14 @@ template <> __device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat
 template <class T> __device__ __forceinline__ T cvt(float v);
 template <> __device__ __forceinline__ float cvt<float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+// whether v, once stored as T, reads back above zero (the test of the backward pass's ReLU mask);
+// for BF16 the sign and magnitude bits of the stored pattern: positive and not zero
+template <class T> __device__ __forceinline__ bool positive_as_stored(float v);
+template <> __device__ __forceinline__ bool positive_as_stored<float>(float v) { return v > 0.f; }
+template <> __device__ __forceinline__ bool positive_as_stored<__nv_bfloat16>(float v)
+{
+    return (int16_t)__bfloat16_as_ushort(__float2bfloat16_rn(v)) > 0;
+}
 
 // ---------------------------------------------------------------- features
 // x[i] = (ln max(P[lo+i], 1e-30) - mean) / (std + 1e-6) over the band; one CTA per gate
@@ -590,8 +598,10 @@ __device__ __forceinline__ void c5_split_store(const float4 (&q)[C5Split<TPC>::P
     }
 }
 
-// FWD: in = BF16 activations [B][32][L], out = BF16 relu(conv + bias).
-// !FWD: in = FP32 gradient [B][32][L], out = FP32 conv masked by mask > 0, no bias.
+// FWD: in = BF16 activations [B][32][L], out = BF16 relu(conv + bias); with BITS (a training pass)
+//   also the ReLU mask, bits[b * L + i] bit co = (stored output [b][co][i] > 0).
+// !FWD: in = FP32 gradient [B][32][L], out = FP32 conv masked by the layer below's ReLU, read as
+//   those bits (one word per position, loaded before the epilogue waits for the tile's MMAs), no bias.
 // wt: GEMM rows [out channel][tap][in channel] (BF16), as for conv_tc_kernel.
 // Persistent: CTA c takes tiles c, c + gridDim.x, ... of the n_rows x ceil(L / CT) tiles (row-major)
 // with a two-deep pipeline over two staging buffers, two TMEM accumulators and two mbarriers.  In
@@ -603,11 +613,11 @@ __device__ __forceinline__ void c5_split_store(const float4 (&q)[C5Split<TPC>::P
 // that uniform) and the tiles left are not written.
 constexpr int C5_CTAS_PER_SM = 2;
 static_assert(C5_CTAS_PER_SM * 2 * C5<C5_TPC>::COLS <= 512, "TMEM columns of the resident CTAs");
-template <bool FWD>
+template <bool FWD, bool BITS = !FWD>
 __global__ void __launch_bounds__(C5<C5_TPC>::THREADS, C5_CTAS_PER_SM) conv_tc05_kernel(const void* __restrict__ in,
                                                                          const __nv_bfloat16* __restrict__ wt,
                                                                          const float* __restrict__ bias,
-                                                                         const __nv_bfloat16* __restrict__ mask, int L,
+                                                                         uint32_t* __restrict__ bits, int L,
                                                                          int n_rows, void* __restrict__ out)
 {
     using G = C5<C5_TPC>;
@@ -713,6 +723,11 @@ __global__ void __launch_bounds__(C5<C5_TPC>::THREADS, C5_CTAS_PER_SM) conv_tc05
         const int buf = k & 1, tn = t + (int)gridDim.x;
         const bool more = tn < n_tiles;
         if (more) load(tn);
+        uint32_t mbits = 0;   // backward: the ReLU mask of this thread's position, in flight during the wait
+        if constexpr (!FWD) {
+            const int b = t / tiles_per_row, i = (t - b * tiles_per_row) * C5_CT + 128 * m + 32 * (warp & 3) + lane;
+            if (i < L) mbits = bits[(size_t)b * L + i];
+        }
         const bool done = isr::mbar_wait(isr::smem_u32(&mbar[buf]), (uint32_t)(k >> 1) & 1u, 1u << 26);
         isr::tmem_fence_after_sync();
         {
@@ -723,17 +738,19 @@ __global__ void __launch_bounds__(C5<C5_TPC>::THREADS, C5_CTAS_PER_SM) conv_tc05
             isr::tmem_wait_ld32(r);
             if (done && i < L) {
                 const size_t row = (size_t)b * CH * L + i;
+                uint32_t fbits = 0;
 #pragma unroll
                 for (int co = 0; co < CH; ++co) {
                     const float v = __uint_as_float(r[co]);
                     if constexpr (FWD) {
-                        static_cast<__nv_bfloat16*>(out)[row + (size_t)co * L] =
-                            __float2bfloat16_rn(fmaxf(v + __ldg(bias + co), 0.f));
+                        const __nv_bfloat16 hv = __float2bfloat16_rn(fmaxf(v + __ldg(bias + co), 0.f));
+                        static_cast<__nv_bfloat16*>(out)[row + (size_t)co * L] = hv;
+                        if constexpr (BITS) fbits |= (uint32_t)((int16_t)__bfloat16_as_ushort(hv) > 0) << co;
                     } else {
-                        static_cast<float*>(out)[row + (size_t)co * L] =
-                            __bfloat162float(mask[row + (size_t)co * L]) > 0.f ? v : 0.f;
+                        static_cast<float*>(out)[row + (size_t)co * L] = (mbits >> co) & 1u ? v : 0.f;
                     }
                 }
+                if constexpr (FWD && BITS) bits[(size_t)b * L + i] = fbits;
             }
         }
         // the other staging buffer and accumulator were last used by tile t - gridDim.x, whose
@@ -1239,10 +1256,25 @@ template <> __device__ __forceinline__ void store_pair<__nv_bfloat16>(__nv_bfloa
 {
     *reinterpret_cast<__nv_bfloat162*>(o) = __floats2bfloat162_rn(a, b);
 }
+// the same, returning in bits 0 / 1 whether a / b read back above zero as stored
+template <class T> __device__ __forceinline__ uint32_t store_pair_signs(T* o, float a, float b);
+template <> __device__ __forceinline__ uint32_t store_pair_signs<float>(float* o, float a, float b)
+{
+    store_pair<float>(o, a, b);
+    return (uint32_t)(a > 0.f) | ((uint32_t)(b > 0.f) << 1);
+}
+template <> __device__ __forceinline__ uint32_t store_pair_signs<__nv_bfloat16>(__nv_bfloat16* o, float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    *reinterpret_cast<__nv_bfloat162*>(o) = h;
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(&h);
+    return (uint32_t)((int16_t)(w & 0xffffu) > 0) | ((uint32_t)((int32_t)w > 0x0000ffff) << 1);
+}
 
-template <class T>
+template <class T, bool BITS>
 __global__ void __launch_bounds__(256) conv1_kernel(const T* __restrict__ x, const T* __restrict__ w1,
-                                                    const float* __restrict__ b1, int L, T* __restrict__ out)
+                                                    const float* __restrict__ b1, int L, T* __restrict__ out,
+                                                    uint32_t* __restrict__ bits)
 {
     __shared__ float xs[L1_CT + KT - 1];
     __shared__ __align__(16) float ws[CH][12];   // W1[co][0..8], b1[co], 0, 0
@@ -1263,6 +1295,7 @@ __global__ void __launch_bounds__(256) conv1_kernel(const T* __restrict__ x, con
 #pragma unroll
     for (int j = 0; j < KT + 1; ++j) xv[j] = xs[p + j];
     const bool pair = i + 1 < L && (L & 1) == 0;   // even row offsets: aligned pair stores
+    uint32_t m0 = 0, m1 = 0;                        // ReLU mask bits of positions i, i + 1 (BITS)
 #pragma unroll 4
     for (int co = 0; co < CH; ++co) {
         const float4 wa = *reinterpret_cast<const float4*>(&ws[co][0]);
@@ -1279,11 +1312,25 @@ __global__ void __launch_bounds__(256) conv1_kernel(const T* __restrict__ x, con
         s1 = fmaxf(s1, 0.f);
         T* o = out + ((size_t)b * CH + co) * L + i;
         if (pair) {
-            store_pair<T>(o, s0, s1);
+            if constexpr (BITS) {
+                const uint32_t sg = store_pair_signs<T>(o, s0, s1);
+                m0 |= (sg & 1u) << co;
+                m1 |= (sg >> 1) << co;
+            } else {
+                store_pair<T>(o, s0, s1);
+            }
         } else {
+            if constexpr (BITS) {
+                m0 |= (uint32_t)positive_as_stored<T>(s0) << co;
+                m1 |= (uint32_t)positive_as_stored<T>(s1) << co;
+            }
             o[0] = cvt<T>(s0);
             if (i + 1 < L) o[1] = cvt<T>(s1);
         }
+    }
+    if constexpr (BITS) {
+        bits[(size_t)b * L + i] = m0;
+        if (i + 1 < L) bits[(size_t)b * L + i + 1] = m1;
     }
 }
 
@@ -1632,6 +1679,9 @@ struct isr_est {
     int c5_slots[2] = {1, 1};                 // persistent tcgen05 convolution CTAs, backward / forward
     int* pidx = nullptr;
     float *da0 = nullptr, *da1 = nullptr; // gradient ping-pong [B][32][L]
+    // tcgen05 engine: ReLU masks of h1..h3 as written by a training forward pass, [3][B][L] words,
+    // bit co of word (b, i) set when h_l[b][co][i] > 0 as stored
+    uint32_t* hbits = nullptr;
 };
 
 namespace {
@@ -1675,12 +1725,13 @@ isr_status set_smem_attrs()
                                      (int)wgrad_tc_smem_bytes()));
         EST_TRY(cudaFuncSetAttribute(wgrad_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)W5_SMEM_LAUNCH));
-        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)C5<C5_TPC>::smem(true)));
+        for (auto k : {conv_tc05_kernel<true, false>, conv_tc05_kernel<true, true>}) {
+            EST_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C5<C5_TPC>::smem(true)));
+            EST_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared));
+        }
         EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)C5<C5_TPC>::smem(false)));
-        EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared));
         EST_TRY(cudaFuncSetAttribute(conv_tc05_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      (int)cudaSharedmemCarveoutMaxShared));
     }
@@ -1704,14 +1755,20 @@ isr_status forward_t(isr_est* e, const float* x, int n, float* pos = nullptr, fl
     }
     const T* wf = static_cast<const T*>(e->wf);
     dim3 grid((L + CT - 1) / CT, n);
-    conv1_kernel<T><<<dim3((L + L1_CT - 1) / L1_CT, n), 256, 0, s>>>(act[0], wf, e->theta + OFF_B1, L, act[1]);
+    // a training pass (no prediction outputs) of the tcgen05 engine leaves the ReLU masks of h1..h3
+    // as bits for the backward-data convolutions
+    auto hbits = [&](int l) -> uint32_t* {
+        return (pos == nullptr && e->hbits && l <= 3) ? e->hbits + (size_t)(l - 1) * e->max_batch * L : nullptr;
+    };
+    (hbits(1) ? conv1_kernel<T, true> : conv1_kernel<T, false>)<<<dim3((L + L1_CT - 1) / L1_CT, n), 256, 0, s>>>(
+        act[0], wf, e->theta + OFF_B1, L, act[1], hbits(1));
     for (int l = 2; l <= 4; ++l) {
         if constexpr (kTensorConv<T>) {
             const T* w = static_cast<const T*>(e->tf) + (size_t)(l - 2) * CH * CH * KT;
             if (e->conv05)
-                conv_tc05_kernel<true><<<conv_tc05_grid(L, n, e->c5_slots[1]), C5<C5_TPC>::THREADS,
-                                         C5<C5_TPC>::smem(true), s>>>(act[l - 1], w, e->theta + b_off(l), nullptr, L, n,
-                                                                      act[l]);
+                (hbits(l) ? conv_tc05_kernel<true, true> : conv_tc05_kernel<true, false>)<<<
+                    conv_tc05_grid(L, n, e->c5_slots[1]), C5<C5_TPC>::THREADS, C5<C5_TPC>::smem(true), s>>>(
+                    act[l - 1], w, e->theta + b_off(l), hbits(l), L, n, act[l]);
             else
                 conv_tc_kernel<true><<<dim3((L + CF_CT - 1) / CF_CT, n), CF_THREADS, tc_smem_bytes(true), s>>>(
                     act[l - 1], w, e->theta + b_off(l), nullptr, L, act[l]);
@@ -1771,7 +1828,8 @@ isr_status backward_t(isr_est* e, int n, const float* fpos, const float* pres)
                 const T* w = static_cast<const T*>(e->tb) + (size_t)(l - 2) * CH * CH * KT;
                 if (e->conv05)
                     conv_tc05_kernel<false><<<conv_tc05_grid(L, n, e->c5_slots[0]), C5<C5_TPC>::THREADS,
-                                              C5<C5_TPC>::smem(false), s>>>(da, w, nullptr, act[l - 1], L, n, dn);
+                                              C5<C5_TPC>::smem(false), s>>>(
+                        da, w, nullptr, e->hbits + (size_t)(l - 2) * e->max_batch * L, L, n, dn);
                 else
                     conv_tc_kernel<false><<<dim3((L + CF_CT - 1) / CF_CT, n), CF_THREADS, tc_smem_bytes(false), s>>>(
                         da, w, nullptr, act[l - 1], L, dn);
@@ -1865,6 +1923,7 @@ isr_status isr_est_create(isr_est** out, int32_t nfft, int32_t band_lo, int32_t 
     A((void**)&e->zidx, 4 * B * nxh);
     A((void**)&e->da0, 4 * B * CH * L);
     A((void**)&e->da1, 4 * B * CH * L);
+    if (e->conv05) A((void**)&e->hbits, 4 * 3 * B * L);
     if (r == cudaSuccess) r = cudaMemset(e->theta, 0, 4 * NPARAM);
     if (r == cudaSuccess) r = cudaMemset(e->m, 0, 4 * NPARAM);
     if (r == cudaSuccess) r = cudaMemset(e->v, 0, 4 * NPARAM);
@@ -1987,7 +2046,7 @@ void isr_est_destroy(isr_est* e)
     cudaStreamSynchronize(e->stream);
     void* ptrs[] = {e->theta, e->m, e->v, e->grad, e->wf, e->wb, e->tf, e->tb, e->act[0], e->act[1], e->act[2], e->act[3],
                     e->act[4], e->z, e->pooled, e->u, e->q, e->loss, e->amax, e->da0, e->da1,
-                    e->pmax, e->pidx, e->psum, e->hscal, e->dpool, e->zmax, e->zidx};
+                    e->pmax, e->pidx, e->psum, e->hscal, e->dpool, e->zmax, e->zidx, e->hbits};
     for (void* p : ptrs) cudaFree(p);
     cudaGetLastError();
     delete e;
