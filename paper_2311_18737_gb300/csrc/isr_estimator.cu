@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdint>
 #include <new>
+#include <type_traits>
 
 #include "isr.h"
 #include "isr_kernels.cuh"
@@ -1164,81 +1165,91 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const TH* __restrict__ h, co
 // Weight gradient of the one-channel first layer:
 //   dW1[co][k] += sum_i da[b][co][i] x[b][i + k - 4],  db1[co] += sum_i da[b][co][i]
 // The n_rows x ceil(L / W1_SPAN) spans, row after row, are split into gridDim.x contiguous ranges
-// (two CTAs per SM: at 128 rows x 4608 positions 45.5 us per launch, against 49.5 us with one and
-// 64.6 us with four, where most CTAs take one span), and a CTA keeps its sums in registers over
-// its spans, so every weight receives one atomic per CTA, not one per span.  Within a span [i0, i0 + W1_SPAN) of row b warp w
-// takes output channels 4 w .. 4 w + 3 and lane l the positions i0 + l + 32 m, so every gradient
-// row is read coalesced straight from global memory and the input row once from shared memory;
-// the sums are reduced across lanes with shuffles at the end.
-constexpr int W1_SPAN = 1024;   // a multiple of 32 x 8 (the step)
+// (two CTAs per SM), and a CTA keeps its sums in registers over its spans.  Lane l is output
+// channel l, so a thread holds only that channel's nine tap sums and its bias sum and the
+// registers go to loads in flight.  Within a span [i0, i0 + W1_SPAN) of row b warp w takes the
+// positions i0 + 128 w .. i0 + 128 w + 127 in two rounds of eight steps of 8 positions: per step a
+// lane reads 8 consecutive positions of its channel's gradient row (two 16-byte loads; a round's
+// loads are all issued before the first is used) and the 16 inputs x[p - 4 .. p + 11] as four
+// 16-byte broadcast reads of the span's input row in shared memory.  At the end the eight warps'
+// sums of each channel are added in shared memory and every weight receives one atomic per CTA.
+constexpr int W1_SPAN = 1024;
+constexpr int W1_STEP = 8;                              // positions per lane and step
+constexpr int W1_U = 8;                                 // steps per round (their loads in flight)
+constexpr int W1_WSPAN = W1_SPAN / 8;                   // positions per warp and span
+static_assert(W1_WSPAN % (W1_STEP * W1_U) == 0, "whole rounds per warp and span");
 
 template <class TH>
-__global__ void __launch_bounds__(256) wgrad1_kernel(const TH* __restrict__ x, const float* __restrict__ da, int L,
-                                                     int n_rows, float* __restrict__ dW, float* __restrict__ db)
+__global__ void __launch_bounds__(256, 2) wgrad1_kernel(const TH* __restrict__ x, const float* __restrict__ da, int L,
+                                                        int n_rows, float* __restrict__ dW, float* __restrict__ db)
 {
-    constexpr int CPW = CH / 8;   // output channels per warp
-    __shared__ float xs[W1_SPAN + KT - 1];
+    __shared__ __align__(16) float xs[W1_SPAN + 16];    // xs[j] = x[b][i0 - 4 + j]
+    __shared__ float red[8][CH * (KT + 1)];             // the warps' sums: [warp][channel][tap, bias]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int spr = (L + W1_SPAN - 1) / W1_SPAN;                 // spans per row
     const int64_t total = (int64_t)n_rows * spr;
     const int q_begin = (int)((int64_t)blockIdx.x * total / gridDim.x);
     const int q_end = (int)((int64_t)(blockIdx.x + 1) * total / gridDim.x);
-    float acc[CPW][KT], dbacc[CPW];
+    float acc[KT], dbacc = 0.f;
 #pragma unroll
-    for (int c = 0; c < CPW; ++c) {
-        dbacc[c] = 0.f;
-#pragma unroll
-        for (int k = 0; k < KT; ++k) acc[c][k] = 0.f;
-    }
+    for (int k = 0; k < KT; ++k) acc[k] = 0.f;
+    const bool vec = (L & 3) == 0;   // 16-byte gradient loads (8-position pieces start at multiples of 8)
     for (int q = q_begin; q < q_end; ++q) {
-    const int b = q / spr, i0 = (q - b * spr) * W1_SPAN, iend = min(L, i0 + W1_SPAN);
-    __syncthreads();   // the previous span's reads of xs are done
-    for (int j = threadIdx.x; j < W1_SPAN + KT - 1; j += 256) {
-        const int pos = i0 - HALF + j;
-        xs[j] = (pos >= 0 && pos < L) ? ld<TH>(x, (size_t)b * L + pos) : 0.f;
-    }
-    __syncthreads();
-    const float* dar = da + ((size_t)b * CH + warp * CPW) * L;
-    // eight positions per lane and step: all 32 gradient loads of a step are in flight together
-    constexpr int U = 8;
-    for (int base = i0; base < iend; base += 32 * U) {
-        float d[CPW][U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = base + lane + 32 * u;
-#pragma unroll
-            for (int c = 0; c < CPW; ++c) d[c][u] = i < iend ? __ldg(dar + (size_t)c * L + i) : 0.f;
+        const int b = q / spr, i0 = (q - b * spr) * W1_SPAN, iend = min(L, i0 + W1_SPAN);
+        __syncthreads();   // the previous span's reads of xs are done
+        for (int j = threadIdx.x; j < W1_SPAN + 16; j += 256) {
+            const int pos = i0 - HALF + j;
+            xs[j] = (pos >= 0 && pos < L) ? ld<TH>(x, (size_t)b * L + pos) : 0.f;
         }
+        __syncthreads();
+        const float* dar = da + ((size_t)b * CH + lane) * L;
+#pragma unroll 1
+        for (int r = 0; r < W1_WSPAN / (W1_STEP * W1_U); ++r) {
+            const int pbase = i0 + warp * W1_WSPAN + r * W1_STEP * W1_U;
+            float d[W1_U][W1_STEP];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int j = base - i0 + lane + 32 * u;   // zero gradient past iend: no effect
-            float xv[KT];
+            for (int u = 0; u < W1_U; ++u) {
+                const int p = pbase + W1_STEP * u;
+                if (vec && p + W1_STEP <= iend) {
+                    const float4 a0 = __ldg(reinterpret_cast<const float4*>(dar + p));
+                    const float4 a1 = __ldg(reinterpret_cast<const float4*>(dar + p + 4));
+                    d[u][0] = a0.x; d[u][1] = a0.y; d[u][2] = a0.z; d[u][3] = a0.w;
+                    d[u][4] = a1.x; d[u][5] = a1.y; d[u][6] = a1.z; d[u][7] = a1.w;
+                } else {
 #pragma unroll
-            for (int k = 0; k < KT; ++k) xv[k] = xs[j + k];
+                    for (int t = 0; t < W1_STEP; ++t) d[u][t] = p + t < iend ? __ldg(dar + p + t) : 0.f;
+                }
+            }
 #pragma unroll
-            for (int c = 0; c < CPW; ++c) {
-                dbacc[c] += d[c][u];
+            for (int u = 0; u < W1_U; ++u) {
+                const int j = pbase + W1_STEP * u - i0;   // zero gradient past iend: no effect
+                const float4* x4 = reinterpret_cast<const float4*>(&xs[j]);
+                float xw[16];
 #pragma unroll
-                for (int k = 0; k < KT; ++k) acc[c][k] = fmaf(d[c][u], xv[k], acc[c][k]);
+                for (int v = 0; v < 4; ++v) {
+                    const float4 t4 = x4[v];
+                    xw[4 * v] = t4.x; xw[4 * v + 1] = t4.y; xw[4 * v + 2] = t4.z; xw[4 * v + 3] = t4.w;
+                }
+#pragma unroll
+                for (int t = 0; t < W1_STEP; ++t) {
+                    const float dv = d[u][t];
+                    dbacc += dv;
+#pragma unroll
+                    for (int k = 0; k < KT; ++k) acc[k] = fmaf(dv, xw[t + k], acc[k]);
+                }
             }
         }
     }
-    }
 #pragma unroll
-    for (int c = 0; c < CPW; ++c) {
+    for (int k = 0; k < KT; ++k) red[warp][lane * (KT + 1) + k] = acc[k];
+    red[warp][lane * (KT + 1) + KT] = dbacc;
+    __syncthreads();
+    for (int e = threadIdx.x; e < CH * (KT + 1); e += 256) {
+        float t = 0.f;
 #pragma unroll
-        for (int k = 0; k < KT; ++k)
-            for (int o = 16; o; o >>= 1) acc[c][k] += __shfl_down_sync(0xffffffffu, acc[c][k], o);
-        for (int o = 16; o; o >>= 1) dbacc[c] += __shfl_down_sync(0xffffffffu, dbacc[c], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int c = 0; c < CPW; ++c) {
-            const int co = warp * CPW + c;
-#pragma unroll
-            for (int k = 0; k < KT; ++k) atomicAdd(&dW[co * KT + k], acc[c][k]);
-            atomicAdd(&db[co], dbacc[c]);
-        }
+        for (int w = 0; w < 8; ++w) t += red[w][e];
+        const int co = e / (KT + 1), k = e - co * (KT + 1);
+        atomicAdd(k < KT ? &dW[co * KT + k] : &db[co], t);
     }
 }
 
@@ -1528,17 +1539,46 @@ __global__ void __launch_bounds__(256) head_bwd_row_kernel(const float* __restri
     __shared__ float du_s[CH];
     const float* zb = z + (size_t)b * L;
     const float y = pres[b], f = fpos[b];
-    // softmax statistics and target normalisation
+    // softmax statistics and target normalisation.  Rows of up to 4 x 256 x RV positions (L a
+    // multiple of 4) are read once, as float4 pieces all in flight together, and kept in registers
+    // for both passes; longer or unaligned rows are read twice with scalar loads.
+    constexpr int RV = 5;
+    const bool in_regs = (L & 3) == 0 && L <= 4 * 256 * RV;
+    float4 zr[RV];
     float m = -INFINITY;
-    for (int i = threadIdx.x; i < L; i += 256) m = fmaxf(m, zb[i]);
+    if (in_regs) {
+#pragma unroll
+        for (int v = 0; v < RV; ++v) {
+            const int i = 4 * (threadIdx.x + 256 * v);
+            zr[v] = i < L ? __ldg(reinterpret_cast<const float4*>(zb + i)) : make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+        }
+#pragma unroll
+        for (int v = 0; v < RV; ++v) m = fmaxf(m, fmaxf(fmaxf(zr[v].x, zr[v].y), fmaxf(zr[v].z, zr[v].w)));
+    } else {
+        for (int i = threadIdx.x; i < L; i += 256) m = fmaxf(m, zb[i]);
+    }
     m = block_max(m, red);
     float se = 0.f, st = 0.f, stz = 0.f;
-    for (int i = threadIdx.x; i < L; i += 256) {
-        se += __expf(zb[i] - m);
+    auto term = [&](int i, float zi) {
+        se += __expf(zi - m);
         const float d = (i - f) / SIGMA_T;
         const float t = __expf(-0.5f * d * d);
         st += t;
-        stz += t * zb[i];
+        stz += t * zi;
+    };
+    if (in_regs) {
+#pragma unroll
+        for (int v = 0; v < RV; ++v) {
+            const int i = 4 * (threadIdx.x + 256 * v);
+            if (i < L) {
+                term(i, zr[v].x);
+                term(i + 1, zr[v].y);
+                term(i + 2, zr[v].z);
+                term(i + 3, zr[v].w);
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < L; i += 256) term(i, zb[i]);
     }
     se = block_sum(se, red);
     st = block_sum(st, red);
@@ -1563,7 +1603,7 @@ __global__ void __launch_bounds__(256) head_bwd_row_kernel(const float* __restri
         sc[2] = loc ? y * invB : 0.f;
         sc[3] = f;
     }
-    // presence MLP backward (threads 0..31)
+    // presence MLP backward (du by threads 0..31; the 32 x 64 weight gradient by all threads)
     if (threadIdx.x < CH) {
         const int j = threadIdx.x;
         const float uj = u[b * CH + j];
@@ -1571,9 +1611,10 @@ __global__ void __launch_bounds__(256) head_bwd_row_kernel(const float* __restri
         const float du = uj > 0.f ? dq * theta[OFF_WB + j] : 0.f;
         du_s[j] = du;
         atomicAdd(&grad[OFF_BA + j], du);
-        for (int e = 0; e < 2 * CH; ++e) atomicAdd(&grad[OFF_WA + j * 2 * CH + e], du * pooled[b * 2 * CH + e]);
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < CH * 2 * CH; e += 256)
+        atomicAdd(&grad[OFF_WA + e], du_s[e / (2 * CH)] * pooled[b * 2 * CH + e % (2 * CH)]);
     if (threadIdx.x < 2 * CH) {
         float s = 0.f;
         for (int j = 0; j < CH; ++j) s = fmaf(du_s[j], theta[OFF_WA + j * 2 * CH + threadIdx.x], s);
@@ -1584,7 +1625,7 @@ __global__ void __launch_bounds__(256) head_bwd_row_kernel(const float* __restri
 // warp w: channels 4w .. 4w+3 of the chunk, lanes along the positions (each warp evaluates dz
 // itself), so a thread keeps four partial dw5 sums and every warp adds its own channels
 template <class T>
-__global__ void __launch_bounds__(256) head_bwd_chunk_kernel(const T* __restrict__ h4, const float* __restrict__ theta,
+__global__ void __launch_bounds__(256, 3) head_bwd_chunk_kernel(const T* __restrict__ h4, const float* __restrict__ theta,
                                                              int L, const float* __restrict__ z,
                                                              const int* __restrict__ amax,
                                                              const float* __restrict__ scal,
@@ -1609,7 +1650,7 @@ __global__ void __launch_bounds__(256) head_bwd_chunk_kernel(const T* __restrict
     const T* hb = h4 + ((size_t)b * CH + warp * 4) * L;
     float* ob = da4 + ((size_t)b * CH + warp * 4) * L;
     // dL/dz once per position (every warp needs it for its four channels)
-    __shared__ float dz_s[HD_CT];
+    __shared__ __align__(16) float dz_s[HD_CT];   // read as float4 by the vector path
     float db5 = 0.f;
     for (int i = i0 + threadIdx.x; i < iend; i += 256) {
         const float d = (i - f) / SIGMA_T;
@@ -1619,25 +1660,87 @@ __global__ void __launch_bounds__(256) head_bwd_chunk_kernel(const T* __restrict
     }
     __syncthreads();
     float dw5[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int i = i0 + lane; i < iend; i += 32) {
-        const float dz = dz_s[i - i0];
+    // one position's four channels: dw5 += dz h, da4 = (w5 dz + mean and max pooling terms) (h > 0)
+    auto position = [&](int i, float dz, const float (&hv)[4], float (&o)[4]) {
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-            const float hv = ld<T>(hb, (size_t)cc * L + i);
-            dw5[cc] = fmaf(dz, hv, dw5[cc]);
+            dw5[cc] = fmaf(dz, hv[cc], dw5[cc]);
             float g = w5[cc] * dz + gmean[cc];
             if (i == am[cc]) g += gmax[cc];
-            ob[(size_t)cc * L + i] = hv > 0.f ? g : 0.f;
+            o[cc] = hv[cc] > 0.f ? g : 0.f;
+        }
+    };
+    constexpr int HV = 8;                       // positions per lane and round (one 16-byte BF16 load)
+    constexpr int HR = HD_CT / (32 * HV);       // rounds per chunk
+    static_assert(HD_CT % (32 * HV) == 0, "whole rounds per chunk");
+    bool vec = false;
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) vec = (L & 7) == 0;
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) if (vec) {
+        // lane takes positions p = i0 + 8 lane + 256 r, 8 at a time; every load of the chunk is
+        // issued before the first is used (iend is a multiple of 8: a piece is whole or absent)
+        uint4 hq[HR][4];
+#pragma unroll
+        for (int r = 0; r < HR; ++r) {
+            const int p = i0 + HV * lane + 32 * HV * r;
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc)
+                hq[r][cc] = p < iend ? *reinterpret_cast<const uint4*>(hb + (size_t)cc * L + p) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int r = 0; r < HR; ++r) {
+            const int p = i0 + HV * lane + 32 * HV * r;
+            if (p >= iend) break;
+            const float4 z0 = *reinterpret_cast<const float4*>(&dz_s[p - i0]);
+            const float4 z1 = *reinterpret_cast<const float4*>(&dz_s[p - i0 + 4]);
+            const float dzv[HV] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+            float o[4][HV];
+#pragma unroll
+            for (int k = 0; k < HV; ++k) {
+                float hv[4], ok[4];
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const uint32_t w = (&hq[r][cc].x)[k >> 1];
+                    hv[cc] = __uint_as_float((k & 1) ? (w & 0xffff0000u) : (w << 16));   // BF16 -> FP32
+                }
+                position(p + k, dzv[k], hv, ok);
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) o[cc][k] = ok[cc];
+            }
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                float4* d = reinterpret_cast<float4*>(ob + (size_t)cc * L + p);
+                d[0] = make_float4(o[cc][0], o[cc][1], o[cc][2], o[cc][3]);
+                d[1] = make_float4(o[cc][4], o[cc][5], o[cc][6], o[cc][7]);
+            }
+        }
+    }
+    if (!vec) {
+        for (int i = i0 + lane; i < iend; i += 32) {
+            float hv[4], o[4];
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) hv[cc] = ld<T>(hb, (size_t)cc * L + i);
+            position(i, dz_s[i - i0], hv, o);
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) ob[(size_t)cc * L + i] = o[cc];
         }
     }
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc)
         for (int o = 16; o; o >>= 1) dw5[cc] += __shfl_down_sync(0xffffffffu, dw5[cc], o);
-    for (int o = 16; o; o >>= 1) db5 += __shfl_down_sync(0xffffffffu, db5, o);
     if (lane == 0) {
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) atomicAdd(&grad[OFF_W5 + warp * 4 + cc], dw5[cc]);
-        atomicAdd(&grad[OFF_B5], db5);   // this warp's positions of the chunk
+    }
+    // db5: one sum per CTA (every CTA adds into the same address, so one atomic each, not one per warp)
+    __shared__ float db5_s[8];
+    for (int o = 16; o; o >>= 1) db5 += __shfl_down_sync(0xffffffffu, db5, o);
+    if (lane == 0) db5_s[warp] = db5;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += db5_s[w];
+        atomicAdd(&grad[OFF_B5], t);   // the chunk's positions
     }
 }
 
