@@ -1368,14 +1368,96 @@ __global__ void __launch_bounds__(256) head_chunk_kernel(const T* __restrict__ h
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float zm = -INFINITY;   // the chunk's largest z and its first position
     int zi = i0;
-    for (int i = i0 + threadIdx.x; i < iend; i += 256) {
-        float s = b5;
+    // BF16 rows with L a multiple of 8 are read once: warp w loads its channels 4w .. 4w + 3 with
+    // 16-byte loads (lane: positions p = i0 + 8 lane + 256 r, all loads issued first), keeps their
+    // max / first arg-max / sum and adds their part of z into zp[w]; z = b5 + the eight parts.
+    // Other rows: z over all channels per position, then each channel's statistics, scalar loads.
+    bool vec = false;
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) vec = (L & 7) == 0;
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) if (vec) {
+        constexpr int HV = 8, HR = HD_CT / (32 * HV);
+        __shared__ __align__(16) float zp[8][HD_CT];
+        const T* hw = hb + (size_t)warp * 4 * L;
+        uint4 hq[HR][4];
+#pragma unroll
+        for (int r = 0; r < HR; ++r) {
+            const int p = i0 + HV * lane + 32 * HV * r;
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc)
+                hq[r][cc] = p < iend ? *reinterpret_cast<const uint4*>(hw + (size_t)cc * L + p) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        float mx[4], sum[4];
+        int mi[4];
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            mx[cc] = -INFINITY;
+            sum[cc] = 0.f;
+            mi[cc] = i0;
+        }
+#pragma unroll
+        for (int r = 0; r < HR; ++r) {
+            const int p = i0 + HV * lane + 32 * HV * r;
+            if (p >= iend) break;
+            float zpart[HV];
+#pragma unroll
+            for (int k = 0; k < HV; ++k) {
+                zpart[k] = 0.f;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const uint32_t w = (&hq[r][cc].x)[k >> 1];
+                    const float v = __uint_as_float((k & 1) ? (w & 0xffff0000u) : (w << 16));   // BF16 -> FP32
+                    zpart[k] = fmaf(w5[warp * 4 + cc], v, zpart[k]);
+                    if (v > mx[cc]) {
+                        mx[cc] = v;
+                        mi[cc] = p + k;
+                    }
+                    sum[cc] += v;
+                }
+            }
+            float4* zq = reinterpret_cast<float4*>(&zp[warp][p - i0]);
+            zq[0] = make_float4(zpart[0], zpart[1], zpart[2], zpart[3]);
+            zq[1] = make_float4(zpart[4], zpart[5], zpart[6], zpart[7]);
+        }
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            for (int o = 16; o; o >>= 1) {
+                const float om = __shfl_down_sync(0xffffffffu, mx[cc], o);
+                const int oi = __shfl_down_sync(0xffffffffu, mi[cc], o);
+                sum[cc] += __shfl_down_sync(0xffffffffu, sum[cc], o);
+                if (om > mx[cc] || (om == mx[cc] && oi < mi[cc])) {
+                    mx[cc] = om;
+                    mi[cc] = oi;
+                }
+            }
+            if (lane == 0) {
+                const size_t o = ((size_t)b * nx + xc) * CH + warp * 4 + cc;
+                pmax[o] = mx[cc];
+                pidx[o] = mi[cc];
+                psum[o] = sum[cc];
+            }
+        }
+        __syncthreads();
+        for (int i = i0 + threadIdx.x; i < iend; i += 256) {
+            float s = b5;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) s += zp[w][i - i0];
+            z[(size_t)b * L + i] = s;
+            if (s > zm) {
+                zm = s;
+                zi = i;
+            }
+        }
+    }
+    if (!vec) {
+        for (int i = i0 + threadIdx.x; i < iend; i += 256) {
+            float s = b5;
 #pragma unroll 8
-        for (int c = 0; c < CH; ++c) s = fmaf(w5[c], ld<T>(hb, (size_t)c * L + i), s);
-        z[(size_t)b * L + i] = s;
-        if (s > zm) {
-            zm = s;
-            zi = i;
+            for (int c = 0; c < CH; ++c) s = fmaf(w5[c], ld<T>(hb, (size_t)c * L + i), s);
+            z[(size_t)b * L + i] = s;
+            if (s > zm) {
+                zm = s;
+                zi = i;
+            }
         }
     }
     for (int o = 16; o; o >>= 1) {
@@ -1402,8 +1484,8 @@ __global__ void __launch_bounds__(256) head_chunk_kernel(const T* __restrict__ h
         zmax[(size_t)b * nx + xc] = zm_s[0];
         zidx[(size_t)b * nx + xc] = zi_s[0];
     }
-    // warp w: channels 4w .. 4w+3
-    for (int cc = 0; cc < 4; ++cc) {
+    // warp w: channels 4w .. 4w+3 (done above for the vector path)
+    if (!vec) for (int cc = 0; cc < 4; ++cc) {
         const int c = warp * 4 + cc;
         float mx = -INFINITY, sum = 0.f;
         int mi = i0;
@@ -1625,7 +1707,7 @@ __global__ void __launch_bounds__(256) head_bwd_row_kernel(const float* __restri
 // warp w: channels 4w .. 4w+3 of the chunk, lanes along the positions (each warp evaluates dz
 // itself), so a thread keeps four partial dw5 sums and every warp adds its own channels
 template <class T>
-__global__ void __launch_bounds__(256, 3) head_bwd_chunk_kernel(const T* __restrict__ h4, const float* __restrict__ theta,
+__global__ void __launch_bounds__(256, 2) head_bwd_chunk_kernel(const T* __restrict__ h4, const float* __restrict__ theta,
                                                              int L, const float* __restrict__ z,
                                                              const int* __restrict__ amax,
                                                              const float* __restrict__ scal,
@@ -1649,6 +1731,24 @@ __global__ void __launch_bounds__(256, 3) head_bwd_chunk_kernel(const T* __restr
     const float* zb = z + (size_t)b * L;
     const T* hb = h4 + ((size_t)b * CH + warp * 4) * L;
     float* ob = da4 + ((size_t)b * CH + warp * 4) * L;
+    // BF16 rows with L a multiple of 8: lane takes positions p = i0 + 8 lane + 256 r, 8 at a time,
+    // and every activation load of the chunk is issued here, before dz is computed (iend is a
+    // multiple of 8: a piece is whole or absent)
+    constexpr int HV = 8;                       // positions per lane and round (one 16-byte BF16 load)
+    constexpr int HR = HD_CT / (32 * HV);       // rounds per chunk
+    static_assert(HD_CT % (32 * HV) == 0, "whole rounds per chunk");
+    bool vec = false;
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) vec = (L & 7) == 0;
+    uint4 hq[HR][4];
+    if (vec) {
+#pragma unroll
+        for (int r = 0; r < HR; ++r) {
+            const int p = i0 + HV * lane + 32 * HV * r;
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc)
+                hq[r][cc] = p < iend ? *reinterpret_cast<const uint4*>(hb + (size_t)cc * L + p) : make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
     // dL/dz once per position (every warp needs it for its four channels)
     __shared__ __align__(16) float dz_s[HD_CT];   // read as float4 by the vector path
     float db5 = 0.f;
@@ -1670,22 +1770,7 @@ __global__ void __launch_bounds__(256, 3) head_bwd_chunk_kernel(const T* __restr
             o[cc] = hv[cc] > 0.f ? g : 0.f;
         }
     };
-    constexpr int HV = 8;                       // positions per lane and round (one 16-byte BF16 load)
-    constexpr int HR = HD_CT / (32 * HV);       // rounds per chunk
-    static_assert(HD_CT % (32 * HV) == 0, "whole rounds per chunk");
-    bool vec = false;
-    if constexpr (std::is_same<T, __nv_bfloat16>::value) vec = (L & 7) == 0;
     if constexpr (std::is_same<T, __nv_bfloat16>::value) if (vec) {
-        // lane takes positions p = i0 + 8 lane + 256 r, 8 at a time; every load of the chunk is
-        // issued before the first is used (iend is a multiple of 8: a piece is whole or absent)
-        uint4 hq[HR][4];
-#pragma unroll
-        for (int r = 0; r < HR; ++r) {
-            const int p = i0 + HV * lane + 32 * HV * r;
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc)
-                hq[r][cc] = p < iend ? *reinterpret_cast<const uint4*>(hb + (size_t)cc * L + p) : make_uint4(0u, 0u, 0u, 0u);
-        }
 #pragma unroll
         for (int r = 0; r < HR; ++r) {
             const int p = i0 + HV * lane + 32 * HV * r;
