@@ -1167,13 +1167,14 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const TH* __restrict__ h, co
 // The n_rows x ceil(L / W1_SPAN) spans, row after row, are split into gridDim.x contiguous ranges
 // (two CTAs per SM), and a CTA keeps its sums in registers over its spans.  Lane l is output
 // channel l, so a thread holds only that channel's nine tap sums and its bias sum and the
-// registers go to loads in flight.  Within a span [i0, i0 + W1_SPAN) of row b warp w takes the
-// positions i0 + 128 w .. i0 + 128 w + 127 in two rounds of eight steps of 8 positions: per step a
+// registers go to loads in flight.  Spans are short (512 positions) so that CTAs get near-equal
+// numbers of them.  Within a span [i0, i0 + W1_SPAN) of row b warp w takes the positions
+// i0 + 64 w .. i0 + 64 w + 63 in rounds of eight steps of 8 positions: per step a
 // lane reads 8 consecutive positions of its channel's gradient row (two 16-byte loads; a round's
 // loads are all issued before the first is used) and the 16 inputs x[p - 4 .. p + 11] as four
 // 16-byte broadcast reads of the span's input row in shared memory.  At the end the eight warps'
 // sums of each channel are added in shared memory and every weight receives one atomic per CTA.
-constexpr int W1_SPAN = 1024;
+constexpr int W1_SPAN = 512;
 constexpr int W1_STEP = 8;                              // positions per lane and step
 constexpr int W1_U = 8;                                 // steps per round (their loads in flight)
 constexpr int W1_WSPAN = W1_SPAN / 8;                   // positions per warp and span
